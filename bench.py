@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the bead-rod BD time step with HI on GB300.
+
+Default workload: 64 chains of N = 1000 beads (D is 3000 x 3000 per chain),
+h* = 0.25, simple shear at Wi = 100 (lambda = 1), dt = 1e-4, seeded random-walk
+initial conformations and N(0,1) noise.  The mixed-precision path is the
+headline; the FP64 path runs the same chains on the same GPU for the ratio.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  Under torchrun every rank advances its
+own replica batch (independent chains, no data exchange: weak scaling); the
+timing barrier is the only collective.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2208_06559_gb300 import inputs  # noqa: E402
+
+METRIC = "chain-timesteps/s at N=1000 (mixed vs FP64, same GPU); Cholesky % tensor peak"
+UNIT = "chain-timesteps/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def workload_cfg(args):
+    w = inputs.WORKLOADS[args.workload]
+    return w
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2208_06559_gb300 as bd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload_cfg(args)
+    Nc = w.lengths()
+    total = int(Nc.sum())
+    seed = w.seed + 1000 * rank          # disjoint replicas per rank
+    r0 = torch.from_numpy(inputs.random_walk(Nc, seed)).to(dev)
+    K, W = args.steps, args.warmup
+    noise_host = inputs.gaussian_noise(K + W, total, seed + 1)
+    noise = torch.from_numpy(noise_host).to(dev)
+    peaks, peak_src = load_peaks()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(prec, nsteps, nwarm):
+        ctx = bd.Context(Nc, h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, precision=prec)
+        ctx.set_state(r0)
+        for i in range(nwarm):
+            ctx.step(noise[i:i + 1])
+        barrier()
+        l0 = ctx.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        ctx.step(noise[nwarm:nwarm + nsteps])
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.kernel_launches() - l0
+        _, st = ctx.observables()
+        return ctx, ms, launches, st
+
+    prec = bd.MIXED_TF32 if w.precision != 0 else bd.FP64
+    with ClockSampler(local_rank) as clk:
+        ctx, ms, launches, st = timed_steps(prec, K, W)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = len(Nc) * K * world / (ms_max / 1e3)
+
+    # Dominant stage: the Cholesky factorisation, timed live with CUDA events
+    # on the launching stream (assembly re-run before each factorisation).
+    reps = 3
+    fms = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.assemble()
+        a.record(stream)
+        ctx.factor()
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms += a.elapsed_time(b)
+    fms /= reps
+    npad = 3 * Nc
+    chol_flops = float(np.sum(npad.astype(np.float64) ** 3) / 3.0)
+    achieved_tf = chol_flops / (fms / 1e3) / 1e12
+    if prec == bd.FP64:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": 1.25, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 (no measured FP64 peak)",
+                "kernel": "cholesky (FP64 SIMT)"}
+    else:
+        tf32 = peaks["bf16_tflops"] * 0.5
+        roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tf32, "unit": "TFLOP/s",
+                "peak_source": f"TF32 = 0.5 x bf16 burst ({peak_src})",
+                "kernel": "cholesky (mixed)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["ms_per_factorisation"] = fms
+    ctx.close()
+
+    # FP64 path on the same chains (the ratio of the metric)
+    fp64 = None
+    if prec != bd.FP64 and not args.skip_fp64:
+        k64 = max(1, min(args.fp64_steps, K))
+        ctx64, ms64, _, st64 = timed_steps(bd.FP64, k64, 1)
+        ctx64.close()
+        v64 = len(Nc) * k64 * world / (ms64 / 1e3)
+        fp64 = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
+                "speedup_mixed_over_fp64": value / v64}
+
+    # End to end through the public API with host buffers: per step the noise
+    # goes host (pinned) -> device and the per-chain observables come back.
+    e2e = None
+    if not args.skip_e2e:
+        ctx = bd.Context(Nc, h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, precision=prec)
+        ctx.set_state(r0)
+        pinned = torch.from_numpy(noise_host).pin_memory()
+        obs_host = torch.empty((len(Nc), bd.OBS_STRIDE), dtype=torch.float64).pin_memory()
+        ctx.step(pinned[0:1])
+        ctx.observables(out=obs_host, with_status=False)
+        barrier()
+        ke = max(1, min(K, args.e2e_steps))
+        t0 = time.perf_counter()
+        for i in range(ke):
+            ctx.step(pinned[W + i:W + i + 1])
+            ctx.observables(out=obs_host, with_status=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ctx.close()
+        e2e = {"value": len(Nc) * ke * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": total * 3 * 8, "d2h_bytes_per_step": len(Nc) * bd.OBS_STRIDE * 8,
+               "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(w, Nc, r0.cpu().numpy(), noise_host, args.cpu_chains)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 storage / tf32 trailing updates / f64 panels and tensions"
+            if prec != bd.FP64 else "f64",
+            "data": "synthetic (seeded random-walk chains, N(0,1) noise)",
+            "config": {"workload": w.name, "n_chains_per_gpu": len(Nc), "n_beads": int(Nc.max()),
+                       "hstar": w.hstar, "dt": w.dt, "flow": ["none", "shear", "uniaxial"][w.flow],
+                       "Wi": w.Wi, "lambda": 1.0, "precision": "mixed_tf32" if prec else "fp64",
+                       "l2": "inputs larger than L2 (per-step matrices %.1f GB)" %
+                             (float(np.sum((np.ceil(3 * Nc / (128 if prec else 32)) *
+                                            (128 if prec else 32)) ** 2)) * (4 if prec else 8) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "fp64": fp64, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+            "chain_status_ok": bool((st == 0).all()),
+        }
+        print(json.dumps(line))
+
+
+def cpu_baseline(w, Nc, r0, noise_host, max_chains):
+    import oracle as orc
+    cores = orc.num_threads()
+    S = int(min(len(Nc), max(1, min(cores, max_chains))))
+    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi)
+    Ns = Nc[:S]
+    rs = r0[: int(Ns.sum())]
+    nz = np.ascontiguousarray(noise_host[:1, : int(Ns.sum())])
+    t0 = time.perf_counter()
+    orc.run(p, Ns, rs, nz)
+    el = time.perf_counter() - t0
+    return {"value": S / el, "unit": UNIT, "cores": min(cores, S), "kind": "oracle",
+            "sample": f"{S} chains x 1 step of the workload (N={int(Nc.max())}), OpenMP over chains"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as orc
+    w = workload_cfg(args)
+    Nc = w.lengths()
+    cores = orc.num_threads()
+    S = int(min(len(Nc), max(1, min(cores, args.cpu_chains))))
+    Ns = Nc[:S]
+    r = inputs.random_walk(Ns, w.seed)
+    noise = inputs.gaussian_noise(args.steps + args.warmup, int(Ns.sum()), w.seed + 1)
+    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi)
+    for i in range(args.warmup):
+        r, *_ = orc.run(p, Ns, r, noise[i:i + 1])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        r, *_ = orc.run(p, Ns, r, noise[args.warmup + i:args.warmup + i + 1])
+    el = time.perf_counter() - t0
+    v = S * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random-walk chains, N(0,1) noise)",
+            "config": {"workload": w.name, "n_chains_sampled": S, "n_beads": int(Nc.max()),
+                       "hstar": w.hstar, "dt": w.dt, "Wi": w.Wi},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": min(cores, S), "kind": "oracle",
+                             "sample": f"{S} of {len(Nc)} chains per step, FP64 CPU oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n1000x64_mixed_shear", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-chains", type=int, default=16)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

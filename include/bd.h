@@ -1,0 +1,166 @@
+/*
+ * bd.h -- C ABI of libbd, the GB300 (sm_103a) library for the per-timestep
+ * hot path of Brownian dynamics of bead-rod polymer chains with hydrodynamic
+ * interaction (HI), after Prakash et al., arXiv 2208.06559.
+ *
+ * One time step of every chain in a batch (Sec. 3; Sec. 4 flowchart):
+ *   1. assemble the 3N x 3N Rotne-Prager-Yamakawa diffusion tensor D from the
+ *      bead positions (Sec. 3 Eqs. (7)-(9));
+ *   2. factor D = B B^T by Cholesky (Sec. 3 Eq. (10));
+ *   3. form the Brownian displacement sqrt(2 dt) B xi (noise term of Eq. (6));
+ *   4. add the flow drift dt kappa.r (Eq. (5)/(6)) and the tension drift
+ *      dt D F(T) (constraint-force term of Eq. (6));
+ *   5. solve for the rod tensions T that keep every rod at unit length (the
+ *      rigid, K* -> infinity limit of the semi-implicit scheme of Eqs. (13)-(17)).
+ *
+ * Conventions.  A chain has N >= 2 beads and N-1 rods; rod k joins bead k to
+ * bead k+1.  Rod length b = 1 and bead mobility kT/zeta = 1, so D_ii = I.
+ * Positions, noise and forces are packed FP64 arrays [sum_c N_c][3]: the
+ * beads of chain c start at bead offset sum_{c'<c} N_c'.
+ *
+ * Memory.  Every pointer argument named *_dev is a device pointer allocated by
+ * the caller (cudaMalloc or a framework allocator); pointers named *_host are
+ * host memory.  bd_step and bd_observables also accept host memory for their
+ * data buffers (detected with cudaPointerGetAttributes) and then copy through
+ * library-owned device staging.  The caller owns every buffer it passes; the
+ * context owns its workspace (matrices, tensions, scratch) and frees it in
+ * bd_destroy.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Device work is enqueued asynchronously on it; calls that return
+ * host results (bd_observables with status_host, bd_factor_residual,
+ * bd_read_matrix, bd_chain_status) synchronise that stream first.
+ *
+ * Errors.  Every int-returning call returns BD_OK (0) or a negative code.
+ * Per-chain failures inside a step (a non-positive Cholesky pivot, a tension
+ * solve that did not converge) do not fail the call: the chain is frozen at
+ * its last good state, its status word records the first error, and the
+ * status words are read with bd_observables or bd_chain_status.  No kernel
+ * traps; every device wait is bounded.
+ */
+#ifndef BD_H
+#define BD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BD_OK 0
+#define BD_ERR_ARG (-1)         /* invalid argument */
+#define BD_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define BD_ERR_OOM (-3)         /* device allocation failed */
+#define BD_ERR_NOT_PD (-4)      /* non-positive or NaN Cholesky pivot */
+#define BD_ERR_CONSTRAINT (-5)  /* tension Newton did not converge */
+#define BD_ERR_TIMEOUT (-6)     /* a bounded device wait expired */
+#define BD_ERR_STATE (-7)       /* call made before bd_set_state */
+
+typedef struct bd_ctx bd_ctx; /* opaque, library-owned */
+
+typedef enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2 } bd_flow;
+/* BD_FP64: every stage in FP64.  BD_MIXED_TF32 / BD_MIXED_BF16: D and B stored
+ * in FP32, Cholesky trailing updates on the tensor cores (TF32 or BF16
+ * operands, FP32 accumulation), FP64 diagonal-block factorisation, one
+ * refinement step on the Brownian displacement, FP64 tension solve. */
+typedef enum { BD_FP64 = 0, BD_MIXED_TF32 = 1, BD_MIXED_BF16 = 2 } bd_precision;
+typedef enum { BD_RIGID = 0 } bd_constraint;
+
+/* Observables written per chain by bd_observables (Sec. 5 Eqs. (25)-(27)). */
+#define BD_OBS_STRIDE 8
+#define BD_OBS_REE_X 0     /* r_{N-1} - r_0, three components */
+#define BD_OBS_R2 3        /* |R_ee|^2 */
+#define BD_OBS_RG2 4       /* radius of gyration squared */
+#define BD_OBS_STRETCH 5   /* |R_ee| / (N-1) */
+#define BD_OBS_MAXDEV 6    /* max_k | |Q_k| - 1 | */
+#define BD_OBS_NEWTON 7    /* Newton updates in the last step */
+
+typedef struct {
+  int n_chains;          /* >= 1 */
+  const int* n_beads;    /* host array [n_chains], each N_c >= 2; uneven allowed */
+  double h_star;         /* HI parameter h* >= 0 (Eqs. (8)-(9)) */
+  double a;              /* bead radius; <= 0 means a = h*; a < h* is rejected */
+  double dt;             /* time step > 0 */
+  int flow;              /* bd_flow */
+  double Wi;             /* Weissenberg number; rate = Wi / lambda */
+  double lambda;         /* relaxation time; <= 0 means 1 */
+  int precision;         /* bd_precision */
+  int constraint;        /* bd_constraint (BD_RIGID) */
+  double tol;            /* Newton tolerance on max_k | |Q_k|^2 - 1 |; <= 0 -> 1e-13 */
+  int max_newton;        /* Newton update cap; <= 0 -> 50 */
+  int refine;            /* mixed precision: 1 = one refinement step on B xi */
+} bd_params;
+
+/* Fill *p with defaults: 1 chain (n_beads NULL), h* = 0.25, a = h*, dt = 1e-4,
+ * no flow, lambda = 1, BD_FP64, tol 1e-13, max_newton 50, refine 1. */
+void bd_params_default(bd_params* p);
+
+/* Create a context on the current CUDA device: validates *p, copies n_beads,
+ * allocates all device workspace.  *out receives the handle (NULL on error).
+ * Errors: BD_ERR_ARG, BD_ERR_OOM, BD_ERR_CUDA. */
+int bd_create(const bd_params* p, bd_ctx** out);
+
+/* Free every resource of the context (NULL is allowed). */
+void bd_destroy(bd_ctx* ctx);
+
+/* Load positions [sum N][3] FP64 (device pointer) into the context and reset
+ * every chain's status word and tensions. */
+int bd_set_state(bd_ctx* ctx, const double* r_dev, void* stream);
+
+/* Copy the current positions [sum N][3] FP64 into r_dev (device pointer). */
+int bd_get_state(bd_ctx* ctx, double* r_dev, void* stream);
+
+/* Advance every chain by n_steps >= 1 time steps.  noise: [n_steps][sum N][3]
+ * FP64 i.i.d. N(0,1) numbers, device or host memory, owned by the caller and
+ * read during the call's stream work (host memory is copied before return of
+ * the staged copies).  Asynchronous; returns BD_OK unless the arguments or a
+ * CUDA call fail.  Errors: BD_ERR_ARG, BD_ERR_STATE, BD_ERR_CUDA. */
+int bd_step(bd_ctx* ctx, int n_steps, const double* noise, void* stream);
+
+/* Per-chain observables [n_chains][BD_OBS_STRIDE] FP64 into obs (device or
+ * host memory).  If status_host is not NULL it receives the n_chains status
+ * words (BD_OK or the first per-chain error) after a stream synchronisation,
+ * and the call returns the most severe of them. */
+int bd_observables(bd_ctx* ctx, double* obs, int* status_host, void* stream);
+
+/* Host copies of the per-chain status words and Newton update counts of the
+ * last step (either pointer may be NULL).  Synchronises the stream and
+ * returns the most severe status. */
+int bd_chain_status(bd_ctx* ctx, int* status_host, int* newton_host, void* stream);
+
+/* Number of kernel launches executed by bd_step on this context since its
+ * creation (the captured step graph's kernels times the steps, plus the
+ * kernels of every executed tension-solve iteration).  Synchronises the
+ * stream. */
+int bd_kernel_launches(bd_ctx* ctx, unsigned long long* out, void* stream);
+
+/* Diagnostic: ||B B^T - D||_F / ||D||_F for one chain, from the factor and
+ * the D currently held by the context (after bd_factor or bd_step), in FP64
+ * on the device.  Synchronises the legacy default stream. */
+int bd_factor_residual(bd_ctx* ctx, int chain, double* rel_fro);
+
+/* ---- stage entry points (one row of the step each; for tests and tools) ---- */
+
+/* Stage 1: D from the current positions (Eqs. (7)-(9)). */
+int bd_assemble(bd_ctx* ctx, void* stream);
+/* Stage 2: Cholesky factor of the assembled D (Eq. (10)). */
+int bd_factor(bd_ctx* ctx, void* stream);
+/* Stage 3: y = sqrt(2 dt) B xi for xi [sum N][3] (device); with mixed
+ * precision and refine = 1 the refined displacement of the library is
+ * returned.  y_dev [sum N][3] FP64. */
+int bd_brownian(bd_ctx* ctx, const double* xi_dev, double* y_dev, void* stream);
+/* Stage 4: u = D f for f [sum N][3] (device), FP64 result. */
+int bd_mobility_apply(bd_ctx* ctx, const double* f_dev, double* u_dev, void* stream);
+/* Stage 5 input/outputs: tensions of the last step, [sum (N-1)] FP64. */
+int bd_get_tensions(bd_ctx* ctx, double* T_dev, void* stream);
+
+/* Copy chain `chain`'s dense n x n (n = 3 N_c) matrix `which` to host FP64
+ * row-major: which = 0 -> D, 1 -> the Cholesky factor B (zeros above the
+ * diagonal).  Synchronises the legacy default stream. */
+int bd_read_matrix(bd_ctx* ctx, int chain, int which, double* out_host);
+
+/* Human-readable text for an error code (static storage). */
+const char* bd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BD_H */

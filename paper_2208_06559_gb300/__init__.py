@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) library for the per-timestep hot path of bead-rod Brownian
+dynamics with hydrodynamic interaction (arXiv 2208.06559).
+
+The compute lives in libbd.so (CUDA kernels behind the C ABI of include/bd.h);
+``binding`` marshals torch tensors into it and ``build`` compiles it.
+"""
+from .binding import (FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL, FP64, MIXED_BF16, MIXED_TF32,
+                      OBS_STRIDE, BDError, Context, lib)
+
+__all__ = ["Context", "BDError", "lib", "FLOW_NONE", "FLOW_SHEAR", "FLOW_UNIAXIAL", "FP64",
+           "MIXED_TF32", "MIXED_BF16", "OBS_STRIDE"]

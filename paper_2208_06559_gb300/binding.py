@@ -1,0 +1,249 @@
+"""Thin Python binding of libbd (include/bd.h): argument marshalling only.
+
+Every stage of the time step runs in the library's CUDA kernels.  PyTorch
+provides device memory (tensors) and streams; nothing here computes physics.
+If libbd.so has not been built, loading raises immediately: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbd.so")
+
+BD_OK = 0
+BD_ERR_ARG = -1
+BD_ERR_CUDA = -2
+BD_ERR_OOM = -3
+BD_ERR_NOT_PD = -4
+BD_ERR_CONSTRAINT = -5
+BD_ERR_TIMEOUT = -6
+BD_ERR_STATE = -7
+
+FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
+FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+OBS_STRIDE = 8
+
+_lib = None
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n_chains", ctypes.c_int),
+        ("n_beads", ctypes.POINTER(ctypes.c_int)),
+        ("h_star", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("flow", ctypes.c_int),
+        ("Wi", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("constraint", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_newton", ctypes.c_int),
+        ("refine", ctypes.c_int),
+    ]
+
+
+EXPORTS = {
+    "bd_params_default": (None, [ctypes.POINTER(Params)]),
+    "bd_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
+    "bd_destroy": (None, [ctypes.c_void_p]),
+    "bd_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "bd_chain_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "bd_factor_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "bd_assemble": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_brownian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "bd_mobility_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "bd_get_tensions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_read_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p]),
+    "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "bd_kernel_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
+                                          ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libbd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class BDError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {lib().bd_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code != BD_OK:
+        raise BDError(code, what)
+    return code
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A batch of bead-rod chains held by one libbd context on one GPU.
+
+    Positions, noise and forces are torch float64 tensors shaped [sum N, 3]
+    (noise [n_steps, sum N, 3]) on the CUDA device, or on the CPU for
+    ``step`` (host noise is copied by the library)."""
+
+    def __init__(self, n_beads: Sequence[int], h_star: float = 0.25, dt: float = 1e-4,
+                 flow: int = FLOW_NONE, Wi: float = 0.0, lam: float = 1.0, a: float = 0.0,
+                 precision: int = FP64, tol: float = 1e-13, max_newton: int = 50,
+                 refine: int = 1):
+        L = lib()
+        self.n_beads = np.ascontiguousarray(np.asarray(n_beads, dtype=np.int32))
+        self.n_chains = int(self.n_beads.shape[0])
+        self.total_beads = int(self.n_beads.sum())
+        self.total_rods = self.total_beads - self.n_chains
+        p = Params()
+        L.bd_params_default(ctypes.byref(p))
+        p.n_chains = self.n_chains
+        p.n_beads = self.n_beads.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        p.h_star, p.a, p.dt = float(h_star), float(a), float(dt)
+        p.flow, p.Wi, p.lambda_ = int(flow), float(Wi), float(lam)
+        p.precision, p.tol, p.max_newton, p.refine = int(precision), float(tol), int(max_newton), int(refine)
+        h = ctypes.c_void_p()
+        _check(L.bd_create(ctypes.byref(p), ctypes.byref(h)), "bd_create")
+        self._h = h
+        self.precision = int(precision)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state ---------------------------------------------------------
+    def set_state(self, r, stream=None):
+        assert r.is_cuda and r.dtype.is_floating_point and r.is_contiguous()
+        _check(lib().bd_set_state(self._h, _ptr(r), _stream(stream)), "bd_set_state")
+
+    def get_state(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.total_beads, 3), dtype=torch.float64, device="cuda")
+        _check(lib().bd_get_state(self._h, _ptr(out), _stream(stream)), "bd_get_state")
+        return out
+
+    # -- the step ------------------------------------------------------
+    def step(self, noise, n_steps: Optional[int] = None, stream=None):
+        """Advance n_steps time steps with noise [n_steps, sum N, 3] (device or host)."""
+        if n_steps is None:
+            n_steps = int(noise.shape[0])
+        assert noise.is_contiguous() and noise.numel() >= n_steps * self.total_beads * 3
+        _check(lib().bd_step(self._h, int(n_steps), _ptr(noise), _stream(stream)), "bd_step")
+
+    def observables(self, out=None, stream=None, with_status: bool = True):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_chains, OBS_STRIDE), dtype=torch.float64, device="cuda")
+        st = np.zeros(self.n_chains, dtype=np.int32) if with_status else None
+        rc = lib().bd_observables(self._h, _ptr(out),
+                                  st.ctypes.data_as(ctypes.c_void_p) if st is not None else None,
+                                  _stream(stream))
+        if rc not in (BD_OK, BD_ERR_NOT_PD, BD_ERR_CONSTRAINT):
+            _check(rc, "bd_observables")
+        return out, st
+
+    def chain_status(self, stream=None):
+        st = np.zeros(self.n_chains, dtype=np.int32)
+        it = np.zeros(self.n_chains, dtype=np.int32)
+        lib().bd_chain_status(self._h, st.ctypes.data_as(ctypes.c_void_p),
+                              it.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+        return st, it
+
+    def kernel_launches(self, stream=None) -> int:
+        v = ctypes.c_ulonglong()
+        _check(lib().bd_kernel_launches(self._h, ctypes.byref(v), _stream(stream)),
+               "bd_kernel_launches")
+        return int(v.value)
+
+    def factor_residual(self, chain: int) -> float:
+        v = ctypes.c_double()
+        _check(lib().bd_factor_residual(self._h, int(chain), ctypes.byref(v)), "bd_factor_residual")
+        return v.value
+
+    # -- stages ----------------------------------------------------------
+    def assemble(self, stream=None):
+        _check(lib().bd_assemble(self._h, _stream(stream)), "bd_assemble")
+
+    def factor(self, stream=None):
+        _check(lib().bd_factor(self._h, _stream(stream)), "bd_factor")
+
+    def brownian(self, xi, stream=None):
+        import torch
+        y = torch.empty_like(xi)
+        _check(lib().bd_brownian(self._h, _ptr(xi), _ptr(y), _stream(stream)), "bd_brownian")
+        return y
+
+    def mobility_apply(self, f, stream=None):
+        import torch
+        u = torch.empty_like(f)
+        _check(lib().bd_mobility_apply(self._h, _ptr(f), _ptr(u), _stream(stream)),
+               "bd_mobility_apply")
+        return u
+
+    def tensions(self, stream=None):
+        import torch
+        T = torch.zeros(max(self.total_rods, 1), dtype=torch.float64, device="cuda")
+        _check(lib().bd_get_tensions(self._h, _ptr(T), _stream(stream)), "bd_get_tensions")
+        return T[: self.total_rods]
+
+    def read_matrix(self, chain: int, which: int) -> np.ndarray:
+        import torch
+        torch.cuda.synchronize()
+        n = 3 * int(self.n_beads[chain])
+        out = np.zeros((n, n), dtype=np.float64)
+        _check(lib().bd_read_matrix(self._h, int(chain), int(which),
+                                    out.ctypes.data_as(ctypes.c_void_p)), "bd_read_matrix")
+        return out

@@ -1,0 +1,111 @@
+// bd_internal.h -- shared definitions of libbd's kernels and runtime.
+//
+// Data layout in HBM (one context = one batch of chains):
+//   * positions r, noise, forces: packed FP64 [sum N][3];
+//   * per chain c one square row-major matrix of order np_c (3 N_c rounded up
+//     to the Cholesky tile) holding, after a step's factorisation, the factor
+//     B = L in the lower triangle (diagonal included) and the diffusion tensor
+//     D in the strict upper triangle.  D's diagonal is 1 (Sec. 3 Eq. (7)) and
+//     is not stored.  Rows and columns past 3 N_c are an identity border, so
+//     the padded matrix factors to diag(L, I);
+//   * per chain a second square matrix of order mp_c (N_c - 1 rounded up to
+//     32) for the rod-coupling matrix K = U^T C^T D C U and its factor;
+//   * FP64 (BD_FP64) or FP32 (mixed) element type for both matrices.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bd.h"
+
+namespace bd {
+
+// Per-chain descriptor (device resident, one per chain).
+struct ChainDesc {
+  int N;           // beads
+  int n;           // 3N
+  int np;          // padded order of the D/L matrix
+  int m;           // rods N-1
+  int mp;          // padded order of K
+  int pad_;
+  long long boff;  // first bead in packed [sum N][3] arrays
+  long long roff;  // first rod in packed [sum (N-1)] arrays
+  long long moff;  // first element of the D/L matrix
+  long long koff;  // first element of K
+  long long soff;  // first element of the SYMV partial-sum scratch
+};
+
+enum NewtonState : int { NS_ACTIVE = 0, NS_EXTRA = 1, NS_DONE = 2, NS_FAILED = 3 };
+
+// Physical parameters read by the kernels (passed by value).
+struct Phys {
+  double hstar, a, dt, sq2dt;
+  double kappa[9];
+  double tol;
+  int max_newton;
+  int n_chains;
+};
+
+// Device-side step arguments (read by the captured step graph each replay).
+struct StepArgs {
+  const double* noise;  // [n_steps][sum N][3]
+  long long stride;     // sum N * 3
+  int step;             // replay index within the current bd_step call
+  int loops_in_step;    // tension-solve loop iterations in the current step
+};
+
+constexpr int kSimtTile = 32;     // SIMT Cholesky tile (FP64, FP32) and K tile
+constexpr int kMixedTile = 128;   // tensor-core Cholesky tile (mixed precision)
+constexpr int kSymvTile = 64;     // SYMV tile
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+// ---- kernel launchers (each enqueues on `s`; return cudaGetLastError) ----
+template <typename T>
+cudaError_t launch_fill_identity_border(T* M, const ChainDesc* cd, int n_chains,
+                                        int max_np, bool k_matrix, cudaStream_t s);
+template <typename T>
+cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_chains,
+                            int max_N, double hstar, double a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_chol_simt(T* M, const ChainDesc* cd, int n_chains, int max_tiles,
+                             bool k_matrix, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trmv(const T* M, const ChainDesc* cd, int n_chains, int max_n,
+                        const double* x, const StepArgs* args, double scale, double* y,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_np,
+                        const double* f, double* scratch, double* u, const int* state,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
+                          const double* u, cudaStream_t s);
+
+cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd,
+                             int n_chains, int max_N, Phys ph, double* rstar,
+                             double* uhat, double* T, double* F, int* state,
+                             const int* status, int* iters, cudaStream_t s);
+cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
+                                   int n_chains, Phys ph, double* rT, double* rhs,
+                                   int* state, int* status, const int* iters,
+                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_newton_solve(const T* K, const ChainDesc* cd, int n_chains, Phys ph,
+                                const double* uhat, double* rhs, double* Tn, double* F,
+                                int* state, int* iters, cudaStream_t s);
+cudaError_t launch_newton_any_active(const int* state, int n_chains,
+                                     cudaGraphConditionalHandle h, unsigned long long* loops,
+                                     StepArgs* args, int max_loops, cudaStream_t s);
+cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_beads,
+                            const double* rT, double* r, const int* state, int* status,
+                            StepArgs* args, cudaStream_t s);
+cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chains,
+                               const int* iters, double* obs, cudaStream_t s);
+cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_extract(const T* M, const ChainDesc* cd, int chain, int which, double* out,
+                           cudaStream_t s);
+
+}  // namespace bd

@@ -1,0 +1,622 @@
+// bd_runtime.cu -- the C ABI of libbd (declared in include/bd.h): context
+// creation and workspace layout, the captured step graph, and the stage
+// entry points.
+//
+// One bd_step replays a CUDA graph once per time step.  The graph holds the
+// whole step for the whole batch: assembly, blocked Cholesky (one group of
+// launches per block column), Brownian displacement, flow predictor, the
+// rod-coupling matrix K and its factor, then a conditional WHILE node whose
+// body (mobility product, residual, solve, condition update) repeats until
+// every chain has converged or failed, and the commit of the new positions.
+// The noise pointer and the step index live in device memory (StepArgs), so
+// the same graph serves every call.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "bd_internal.h"
+
+using namespace bd;
+
+struct bd_ctx {
+  int device = 0;
+  bd_params p{};
+  std::vector<int> Nc;
+  int n_chains = 0;
+  long long total_beads = 0, total_rods = 0;
+  int max_N = 0, max_n = 0, max_np = 0, max_m = 0, max_mp = 0;
+  bool mixed = false;
+  int tileM = kSimtTile;
+  Phys ph{};
+  std::vector<ChainDesc> h_cd;
+  ChainDesc* d_cd = nullptr;
+  void* M = nullptr;
+  size_t M_elems = 0;
+  void* K = nullptr;
+  size_t K_elems = 0;
+  size_t elem = 8;
+  double *r = nullptr, *rstar = nullptr, *rT = nullptr, *y = nullptr, *u = nullptr, *F = nullptr;
+  double *uhat = nullptr, *T = nullptr, *rhs = nullptr, *scratch = nullptr, *obs = nullptr;
+  double* stage = nullptr;  // staging for host-memory noise / observables
+  size_t stage_elems = 0;
+  int *status = nullptr, *state = nullptr, *iters = nullptr;
+  StepArgs* args = nullptr;
+  unsigned long long* loops = nullptr;  // Newton loop-body executions (device counter)
+  unsigned long long steps_launched = 0;
+  size_t graph_kernels = 0, body_kernels = 0;
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool have_state = false;
+  std::mutex mu;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      fprintf(stderr, "libbd: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
+              __FILE__, __LINE__);                                                \
+      return BD_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+template <typename T>
+int enqueue_factor_t(bd_ctx* c, cudaStream_t s) {
+  T* M = static_cast<T*>(c->M);
+  // Tensor-core path for mixed precision is selected in chol_dispatch.
+  CK(launch_chol_simt<T>(M, c->d_cd, c->n_chains, c->max_np / kSimtTile, false, c->status, s));
+  return BD_OK;
+}
+
+int enqueue_assemble(bd_ctx* c, cudaStream_t s) {
+  const double a = c->ph.a;
+  if (c->mixed)
+    CK(launch_assemble<float>(c->r, (float*)c->M, c->d_cd, c->n_chains, c->max_N, c->ph.hstar, a, s));
+  else
+    CK(launch_assemble<double>(c->r, (double*)c->M, c->d_cd, c->n_chains, c->max_N, c->ph.hstar, a, s));
+  return BD_OK;
+}
+
+int enqueue_factor(bd_ctx* c, cudaStream_t s) {
+  return c->mixed ? enqueue_factor_t<float>(c, s) : enqueue_factor_t<double>(c, s);
+}
+
+// y = sqrt(2 dt) B xi; xi from `x` or, when args != NULL, from the step's
+// slice of the noise array.
+int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y, cudaStream_t s) {
+  const double sc = c->ph.sq2dt;
+  if (c->mixed)
+    CK(launch_trmv<float>((const float*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
+  else
+    CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
+  return BD_OK;
+}
+
+int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaStream_t s) {
+  if (c->mixed)
+    CK(launch_symv<float>((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
+                          state, s));
+  else
+    CK(launch_symv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
+                           state, s));
+  return BD_OK;
+}
+
+int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
+  int rc;
+  if ((rc = enqueue_assemble(c, s))) return rc;
+  if ((rc = enqueue_factor(c, s))) return rc;
+  if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
+  CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
+                      c->F, c->state, c->status, c->iters, s));
+  if (c->mixed) {
+    CK(launch_form_k<float>((const float*)c->M, (float*)c->K, c->d_cd, c->n_chains, c->max_m,
+                            c->uhat, s));
+    CK(launch_chol_simt<float>((float*)c->K, c->d_cd, c->n_chains, c->max_mp / kSimtTile, true,
+                               c->status, s));
+  } else {
+    CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
+                             c->uhat, s));
+    CK(launch_chol_simt<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp / kSimtTile, true,
+                                c->status, s));
+  }
+  return BD_OK;
+}
+
+int enqueue_newton_body(bd_ctx* c, cudaGraphConditionalHandle h, cudaStream_t s) {
+  int rc;
+  if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+  CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
+                            c->status, c->iters, s));
+  if (c->mixed)
+    CK(launch_newton_solve<float>((const float*)c->K, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
+                                  c->T, c->F, c->state, c->iters, s));
+  else
+    CK(launch_newton_solve<double>((const double*)c->K, c->d_cd, c->n_chains, c->ph, c->uhat,
+                                   c->rhs, c->T, c->F, c->state, c->iters, s));
+  CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->ph.max_newton + 3, s));
+  return BD_OK;
+}
+
+size_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  size_t k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+int build_step_graph(bd_ctx* c) {
+  if (c->exec) return BD_OK;
+  cudaStream_t s = c->cs;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_pre_newton(c, s);
+  cudaGraph_t g = nullptr;
+  if (rc) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t cg = nullptr;
+  CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+  // cudaGraphNodeParams holds a union without a default constructor
+  alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
+  memset(cp_buf, 0, sizeof(cp_buf));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_buf);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->cs2, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  rc = enqueue_newton_body(c, h, c->cs2);
+  cudaGraph_t body_out = nullptr;
+  CK(cudaStreamEndCapture(c->cs2, &body_out));
+  if (rc) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
+                     c->args, s));
+  CK(cudaStreamEndCapture(s, &g));
+  c->graph = g;
+  c->graph_kernels = count_kernel_nodes(g);
+  c->body_kernels = count_kernel_nodes(body);
+  CK(cudaGraphInstantiate(&c->exec, g, 0));
+  return BD_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure_stage(bd_ctx* c, size_t elems) {
+  if (c->stage_elems >= elems) return BD_OK;
+  if (c->stage) cudaFree(c->stage);
+  c->stage = nullptr;
+  c->stage_elems = 0;
+  if (cudaMalloc(&c->stage, elems * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return BD_ERR_OOM;
+  }
+  c->stage_elems = elems;
+  return BD_OK;
+}
+
+int worst(const int* st, int n) {
+  int w = BD_OK;
+  for (int i = 0; i < n; ++i)
+    if (st[i] != BD_OK && (w == BD_OK || st[i] < w)) w = st[i];
+  return w;
+}
+
+template <typename T>
+__global__ void k_residual_fro(const T* M, const ChainDesc* cd, int chain, double* acc) {
+  const ChainDesc d = cd[chain];
+  const T* base = M + d.moff;
+  const long long np = d.np;
+  double num = 0.0, den = 0.0;
+  const long long total = (long long)d.n * (d.n + 1) / 2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((long long)i * (i + 1) / 2 > e) --i;
+    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = (int)(e - (long long)i * (i + 1) / 2);  // j <= i
+    double s = 0.0;
+    for (int k = 0; k <= j; ++k) s += (double)base[i * np + k] * (double)base[j * np + k];
+    const double dij = (i == j) ? 1.0 : (double)base[(long long)j * np + i];
+    const double w = (i == j) ? 1.0 : 2.0;
+    num += w * (s - dij) * (s - dij);
+    den += w * dij * dij;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, num);
+    atomicAdd(acc + 1, den);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void bd_params_default(bd_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->n_chains = 1;
+  p->n_beads = nullptr;
+  p->h_star = 0.25;
+  p->a = 0.0;
+  p->dt = 1e-4;
+  p->flow = BD_FLOW_NONE;
+  p->Wi = 0.0;
+  p->lambda = 1.0;
+  p->precision = BD_FP64;
+  p->constraint = BD_RIGID;
+  p->tol = 1e-13;
+  p->max_newton = 50;
+  p->refine = 1;
+}
+
+const char* bd_strerror(int code) {
+  switch (code) {
+    case BD_OK: return "ok";
+    case BD_ERR_ARG: return "invalid argument";
+    case BD_ERR_CUDA: return "CUDA runtime error";
+    case BD_ERR_OOM: return "device allocation failed";
+    case BD_ERR_NOT_PD: return "diffusion tensor not positive definite (Cholesky pivot <= 0 or NaN)";
+    case BD_ERR_CONSTRAINT: return "rod-tension Newton did not converge";
+    case BD_ERR_TIMEOUT: return "bounded device wait expired";
+    case BD_ERR_STATE: return "no state loaded (call bd_set_state first)";
+    default: return "unknown error";
+  }
+}
+
+void bd_destroy(bd_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
+                  c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
+                  c->stage, c->status, c->state, c->iters, c->args, c->loops};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->cs) cudaStreamDestroy(c->cs);
+  if (c->cs2) cudaStreamDestroy(c->cs2);
+  delete c;
+}
+
+int bd_create(const bd_params* p, bd_ctx** out) {
+  if (!out) return BD_ERR_ARG;
+  *out = nullptr;
+  if (!p || p->n_chains < 1 || !p->n_beads) return BD_ERR_ARG;
+  if (!(p->dt > 0.0) || !(p->h_star >= 0.0)) return BD_ERR_ARG;
+  const double a = p->a > 0.0 ? p->a : p->h_star;
+  if (p->h_star > 0.0 && a < p->h_star) return BD_ERR_ARG;  // D may not be positive definite
+  if (p->flow < BD_FLOW_NONE || p->flow > BD_FLOW_UNIAXIAL) return BD_ERR_ARG;
+  if (p->precision < BD_FP64 || p->precision > BD_MIXED_BF16) return BD_ERR_ARG;
+  if (p->constraint != BD_RIGID) return BD_ERR_ARG;
+  for (int i = 0; i < p->n_chains; ++i)
+    if (p->n_beads[i] < 2 || p->n_beads[i] > (1 << 20)) return BD_ERR_ARG;
+
+  bd_ctx* c = new (std::nothrow) bd_ctx();
+  if (!c) return BD_ERR_OOM;
+  cudaGetDevice(&c->device);
+  c->p = *p;
+  c->Nc.assign(p->n_beads, p->n_beads + p->n_chains);
+  c->p.n_beads = c->Nc.data();
+  c->n_chains = p->n_chains;
+  c->mixed = p->precision != BD_FP64;
+  c->tileM = c->mixed ? kMixedTile : kSimtTile;
+  c->elem = c->mixed ? sizeof(float) : sizeof(double);
+
+  Phys& ph = c->ph;
+  ph.hstar = p->h_star;
+  ph.a = a > 0.0 ? a : 1.0;
+  ph.dt = p->dt;
+  ph.sq2dt = sqrt(2.0 * p->dt);
+  const double rate = p->Wi / (p->lambda > 0.0 ? p->lambda : 1.0);
+  for (int q = 0; q < 9; ++q) ph.kappa[q] = 0.0;
+  if (p->flow == BD_FLOW_UNIAXIAL) {
+    ph.kappa[0] = rate;
+    ph.kappa[4] = -0.5 * rate;
+    ph.kappa[8] = -0.5 * rate;
+  } else if (p->flow == BD_FLOW_SHEAR) {
+    ph.kappa[1] = rate;
+  }
+  ph.tol = p->tol > 0.0 ? p->tol : 1e-13;
+  ph.max_newton = p->max_newton > 0 ? p->max_newton : 50;
+  ph.n_chains = c->n_chains;
+
+  long long boff = 0, roff = 0, moff = 0, koff = 0, soff = 0;
+  c->h_cd.resize(c->n_chains);
+  for (int i = 0; i < c->n_chains; ++i) {
+    ChainDesc& d = c->h_cd[i];
+    memset(&d, 0, sizeof(d));
+    d.N = c->Nc[i];
+    d.n = 3 * d.N;
+    d.np = (int)round_up(d.n, c->tileM);
+    d.m = d.N - 1;
+    d.mp = (int)round_up(d.m, kSimtTile);
+    d.boff = boff;
+    d.roff = roff;
+    d.moff = moff;
+    d.koff = koff;
+    d.soff = soff;
+    const long long tsn = ceil_div(d.n, kSymvTile);
+    boff += d.N;
+    roff += d.m;
+    moff += (long long)d.np * d.np;
+    koff += (long long)d.mp * d.mp;
+    soff += tsn * tsn * kSymvTile;
+    c->max_N = d.N > c->max_N ? d.N : c->max_N;
+    c->max_n = d.n > c->max_n ? d.n : c->max_n;
+    c->max_np = d.np > c->max_np ? d.np : c->max_np;
+    c->max_m = d.m > c->max_m ? d.m : c->max_m;
+    c->max_mp = d.mp > c->max_mp ? d.mp : c->max_mp;
+  }
+  c->total_beads = boff;
+  c->total_rods = roff;
+  c->M_elems = (size_t)moff;
+  c->K_elems = (size_t)koff;
+
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  const size_t b3 = (size_t)boff * 3 * sizeof(double);
+  const size_t rr = (size_t)(roff > 0 ? roff : 1) * sizeof(double);
+  bool ok = alloc((void**)&c->d_cd, sizeof(ChainDesc) * c->n_chains) &&
+            alloc(&c->M, c->M_elems * c->elem) && alloc(&c->K, c->K_elems * c->elem) &&
+            alloc((void**)&c->r, b3) && alloc((void**)&c->rstar, b3) && alloc((void**)&c->rT, b3) &&
+            alloc((void**)&c->y, b3) && alloc((void**)&c->u, b3) && alloc((void**)&c->F, b3) &&
+            alloc((void**)&c->uhat, 3 * rr) && alloc((void**)&c->T, rr) && alloc((void**)&c->rhs, rr) &&
+            alloc((void**)&c->scratch, (size_t)(soff > 0 ? soff : 1) * sizeof(double)) &&
+            alloc((void**)&c->obs, (size_t)c->n_chains * BD_OBS_STRIDE * sizeof(double)) &&
+            alloc((void**)&c->status, sizeof(int) * c->n_chains) &&
+            alloc((void**)&c->state, sizeof(int) * c->n_chains) &&
+            alloc((void**)&c->iters, sizeof(int) * c->n_chains) &&
+            alloc((void**)&c->args, sizeof(StepArgs)) &&
+            alloc((void**)&c->loops, sizeof(unsigned long long));
+  if (!ok) {
+    bd_destroy(c);
+    return BD_ERR_OOM;
+  }
+  auto fail = [&](int code) {
+    bd_destroy(c);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(BD_ERR_CUDA);
+  cudaStream_t s = c->cs;
+  if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(c->M, 0, c->M_elems * c->elem, s) != cudaSuccess ||
+      cudaMemsetAsync(c->K, 0, c->K_elems * c->elem, s) != cudaSuccess ||
+      cudaMemsetAsync(c->status, 0, sizeof(int) * c->n_chains, s) != cudaSuccess ||
+      cudaMemsetAsync(c->iters, 0, sizeof(int) * c->n_chains, s) != cudaSuccess ||
+      cudaMemsetAsync(c->T, 0, rr, s) != cudaSuccess ||
+      cudaMemsetAsync(c->args, 0, sizeof(StepArgs), s) != cudaSuccess ||
+      cudaMemsetAsync(c->loops, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return fail(BD_ERR_CUDA);
+  cudaError_t e1, e2;
+  if (c->mixed) {
+    e1 = launch_fill_identity_border<float>((float*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
+    e2 = launch_fill_identity_border<float>((float*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
+  } else {
+    e1 = launch_fill_identity_border<double>((double*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
+    e2 = launch_fill_identity_border<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
+  }
+  if (e1 != cudaSuccess || e2 != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(BD_ERR_CUDA);
+  *out = c;
+  return BD_OK;
+}
+
+int bd_set_state(bd_ctx* c, const double* r_dev, void* stream) {
+  if (!c || !r_dev) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(c->r, r_dev, (size_t)c->total_beads * 3 * sizeof(double),
+                     cudaMemcpyDefault, s));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int) * c->n_chains, s));
+  CK(cudaMemsetAsync(c->iters, 0, sizeof(int) * c->n_chains, s));
+  CK(cudaMemsetAsync(c->T, 0, (size_t)(c->total_rods > 0 ? c->total_rods : 1) * sizeof(double), s));
+  c->have_state = true;
+  return BD_OK;
+}
+
+int bd_get_state(bd_ctx* c, double* r_dev, void* stream) {
+  if (!c || !r_dev) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  CK(cudaMemcpyAsync(r_dev, c->r, (size_t)c->total_beads * 3 * sizeof(double), cudaMemcpyDefault,
+                     (cudaStream_t)stream));
+  return BD_OK;
+}
+
+int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
+  if (!c || n_steps < 1 || !noise) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = build_step_graph(c);
+  if (rc) return rc;
+  const long long stride = c->total_beads * 3;
+  const double* nz = noise;
+  if (!is_device_ptr(noise)) {
+    if ((rc = ensure_stage(c, (size_t)stride * n_steps))) return rc;
+    CK(cudaMemcpyAsync(c->stage, noise, (size_t)stride * n_steps * sizeof(double),
+                       cudaMemcpyHostToDevice, s));
+    nz = c->stage;
+  }
+  CK(launch_set_args(c->args, nz, stride, s));
+  for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, s));
+  c->steps_launched += (unsigned long long)n_steps;
+  return BD_OK;
+}
+
+int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
+  if (!c || !out) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  unsigned long long loops = 0;
+  CK(cudaMemcpyAsync(&loops, c->loops, sizeof(loops), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  // set_args launches once per bd_step call; it is not counted here
+  *out = c->steps_launched * (unsigned long long)c->graph_kernels +
+         loops * (unsigned long long)c->body_kernels;
+  return BD_OK;
+}
+
+int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
+  if (!c) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_observables(c->r, c->d_cd, c->n_chains, c->iters, c->obs, s));
+  if (obs)
+    CK(cudaMemcpyAsync(obs, c->obs, (size_t)c->n_chains * BD_OBS_STRIDE * sizeof(double),
+                       cudaMemcpyDefault, s));
+  if (status_host) {
+    CK(cudaMemcpyAsync(status_host, c->status, sizeof(int) * c->n_chains, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return worst(status_host, c->n_chains);
+  }
+  return BD_OK;
+}
+
+int bd_chain_status(bd_ctx* c, int* status_host, int* newton_host, void* stream) {
+  if (!c) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> st(c->n_chains);
+  CK(cudaMemcpyAsync(st.data(), c->status, sizeof(int) * c->n_chains, cudaMemcpyDeviceToHost, s));
+  if (newton_host)
+    CK(cudaMemcpyAsync(newton_host, c->iters, sizeof(int) * c->n_chains, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (status_host) memcpy(status_host, st.data(), sizeof(int) * c->n_chains);
+  return worst(st.data(), c->n_chains);
+}
+
+int bd_assemble(bd_ctx* c, void* stream) {
+  if (!c) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  return enqueue_assemble(c, (cudaStream_t)stream);
+}
+
+int bd_factor(bd_ctx* c, void* stream) {
+  if (!c) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return enqueue_factor(c, (cudaStream_t)stream);
+}
+
+int bd_brownian(bd_ctx* c, const double* xi_dev, double* y_dev, void* stream) {
+  if (!c || !xi_dev || !y_dev) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return enqueue_brownian(c, xi_dev, nullptr, y_dev, (cudaStream_t)stream);
+}
+
+int bd_mobility_apply(bd_ctx* c, const double* f_dev, double* u_dev, void* stream) {
+  if (!c || !f_dev || !u_dev) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return enqueue_symv(c, f_dev, u_dev, nullptr, (cudaStream_t)stream);
+}
+
+int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
+  if (!c || !T_dev) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (c->total_rods > 0)
+    CK(cudaMemcpyAsync(T_dev, c->T, (size_t)c->total_rods * sizeof(double), cudaMemcpyDefault,
+                       (cudaStream_t)stream));
+  return BD_OK;
+}
+
+int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
+  if (!c || !out_host || chain < 0 || chain >= c->n_chains || (which != 0 && which != 1))
+    return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  const int n = c->h_cd[chain].n;
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, (size_t)n * n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return BD_ERR_OOM;
+  }
+  cudaError_t e = c->mixed ? launch_extract<float>((const float*)c->M, c->d_cd, chain, which, tmp, 0)
+                           : launch_extract<double>((const double*)c->M, c->d_cd, chain, which, tmp, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out_host, tmp, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return e == cudaSuccess ? BD_OK : BD_ERR_CUDA;
+}
+
+int bd_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
+  if (!c || !rel_fro || chain < 0 || chain >= c->n_chains) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  double* acc = nullptr;
+  if (cudaMalloc(&acc, 2 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return BD_ERR_OOM;
+  }
+  cudaMemset(acc, 0, 2 * sizeof(double));
+  if (c->mixed)
+    k_residual_fro<float><<<1024, 256>>>((const float*)c->M, c->d_cd, chain, acc);
+  else
+    k_residual_fro<double><<<1024, 256>>>((const double*)c->M, c->d_cd, chain, acc);
+  double h[2] = {0, 0};
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(h, acc, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(acc);
+  if (e != cudaSuccess) return BD_ERR_CUDA;
+  *rel_fro = sqrt(h[0] / h[1]);
+  return BD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// k_assemble.cu -- RPY diffusion-tensor assembly (Sec. 3 Eqs. (7)-(9)).
+//
+// The paper's "Diffusion Tensor" kernel (Sec. 4) releases one thread per
+// scalar element of the dense 3(N+1) x 3(N+1) matrix and branches on i == j.
+// Here one thread evaluates one 3x3 bead-pair block (the separation, its norm
+// and the two RPY coefficients are shared by the nine elements), a CTA stages
+// a 16 x 16 bead tile (48 x 48 elements) in shared memory, and the tile is
+// written twice with coalesced row stores: once at (i, j) and once transposed
+// at (j, i).  The result is the full symmetric D in the chain's row-major
+// matrix; the Cholesky later overwrites the lower triangle with the factor and
+// the strict upper triangle keeps D.
+#include "bd_internal.h"
+
+namespace bd {
+
+constexpr int kBeadTile = 16;
+constexpr int kElTile = 3 * kBeadTile;
+
+// Coefficients of D_ij = cI * I + cRR * R R^T for separation R (|R|^2 = R2).
+// Eq. (8) for R >= 2a, Eq. (9) for R < 2a, the overlap limit (h*/a) I at R = 0.
+template <typename C>
+__device__ __forceinline__ void rpy_coeffs(C R2, C hstar, C a, C& cI, C& cRR) {
+  const C Rn = sqrt(R2);
+  if (hstar == C(0)) {
+    cI = C(0);
+    cRR = C(0);
+  } else if (Rn >= C(2) * a) {
+    const C pref = C(0.75) * hstar / Rn;
+    const C a2R2 = a * a / R2;
+    cI = pref * (C(1) + C(2) / C(3) * a2R2);
+    cRR = pref * (C(1) - C(2) * a2R2) / R2;
+  } else {
+    const C pref = C(0.375) * hstar / a;
+    cI = pref * (C(8) / C(3) - C(0.75) * Rn / a);
+    cRR = (Rn > C(0)) ? pref * (C(0.25) / a) / Rn : C(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, T* __restrict__ M,
+                                                  const ChainDesc* __restrict__ cd, double hstar,
+                                                  double a) {
+  using C = T;  // arithmetic type of the coefficients (FP64 or FP32)
+  __shared__ T S[kElTile][kElTile + 1];
+  const ChainDesc d = cd[blockIdx.y];
+  const int TB = (d.N + kBeadTile - 1) / kBeadTile;
+  const int p = blockIdx.x;
+  if (p >= TB * (TB + 1) / 2) return;
+  int bi = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  while (bi * (bi + 1) / 2 > p) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= p) ++bi;
+  const int bj = p - bi * (bi + 1) / 2;  // bj <= bi
+
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = bi * kBeadTile + ty, j = bj * kBeadTile + tx;
+  T blk[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) blk[q] = T(0);
+  if (i < d.N && j < d.N) {
+    if (i == j) {
+      blk[0] = blk[4] = blk[8] = T(1);
+    } else {
+      const double* ri = r + 3 * (d.boff + i);
+      const double* rj = r + 3 * (d.boff + j);
+      const double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
+      const C R[3] = {(C)dx, (C)dy, (C)dz};
+      const C R2 = (C)(dx * dx + dy * dy + dz * dz);
+      C cI, cRR;
+      rpy_coeffs<C>(R2, (C)hstar, (C)a, cI, cRR);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) blk[3 * k + l] = (k == l ? cI : C(0)) + cRR * R[k] * R[l];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) S[3 * ty + k][3 * tx + l] = blk[3 * k + l];
+  __syncthreads();
+
+  T* base = M + d.moff;
+  const long long np = d.np;
+  const int r0 = kElTile * bi, c0 = kElTile * bj;
+  for (int e = threadIdx.x; e < kElTile * kElTile; e += blockDim.x) {
+    const int rr = e / kElTile, cc = e % kElTile;
+    const int row = r0 + rr, col = c0 + cc;
+    if (row < d.n && col < d.n) base[row * np + col] = S[rr][cc];
+  }
+  if (bi != bj) {
+    for (int e = threadIdx.x; e < kElTile * kElTile; e += blockDim.x) {
+      const int rr = e / kElTile, cc = e % kElTile;
+      const int row = c0 + rr, col = r0 + cc;
+      if (row < d.n && col < d.n) base[row * np + col] = S[cc][rr];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_chains, int max_N,
+                            double hstar, double a, cudaStream_t s) {
+  const int TB = (max_N + kBeadTile - 1) / kBeadTile;
+  dim3 grid(TB * (TB + 1) / 2, n_chains);
+  k_assemble<T><<<grid, 256, 0, s>>>(r, M, cd, hstar, a);
+  return cudaGetLastError();
+}
+
+// Identity border of a padded matrix: ones on the diagonal past the logical
+// order (the rest of the border is zeroed by a memset at creation).
+template <typename T>
+__global__ void k_border(T* M, const ChainDesc* cd, bool kmat) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int n = kmat ? d.m : d.n, np = kmat ? d.mp : d.np;
+  T* base = M + (kmat ? d.koff : d.moff);
+  for (int q = n + blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x)
+    base[(long long)q * np + q] = T(1);
+}
+
+template <typename T>
+cudaError_t launch_fill_identity_border(T* M, const ChainDesc* cd, int n_chains, int max_np,
+                                        bool kmat, cudaStream_t s) {
+  (void)max_np;
+  k_border<T><<<dim3(1, n_chains), 128, 0, s>>>(M, cd, kmat);
+  return cudaGetLastError();
+}
+
+// Dense FP64 copy of D (which = 0) or of the factor B (which = 1) of one chain.
+template <typename T>
+__global__ void k_extract(const T* M, const ChainDesc* cd, int chain, int which, double* out) {
+  const ChainDesc d = cd[chain];
+  const T* base = M + d.moff;
+  const long long total = (long long)d.n * d.n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / d.n), c = (int)(e % d.n);
+    double v;
+    if (which == 0) {
+      v = (r == c) ? 1.0 : (double)(r < c ? base[(long long)r * d.np + c] : base[(long long)c * d.np + r]);
+    } else {
+      v = (r >= c) ? (double)base[(long long)r * d.np + c] : 0.0;
+    }
+    out[e] = v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_extract(const T* M, const ChainDesc* cd, int chain, int which, double* out,
+                           cudaStream_t s) {
+  k_extract<T><<<256, 256, 0, s>>>(M, cd, chain, which, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_assemble<double>(const double*, double*, const ChainDesc*, int, int,
+                                             double, double, cudaStream_t);
+template cudaError_t launch_assemble<float>(const double*, float*, const ChainDesc*, int, int,
+                                            double, double, cudaStream_t);
+template cudaError_t launch_fill_identity_border<double>(double*, const ChainDesc*, int, int, bool,
+                                                         cudaStream_t);
+template cudaError_t launch_fill_identity_border<float>(float*, const ChainDesc*, int, int, bool,
+                                                        cudaStream_t);
+template cudaError_t launch_extract<double>(const double*, const ChainDesc*, int, int, double*,
+                                            cudaStream_t);
+template cudaError_t launch_extract<float>(const float*, const ChainDesc*, int, int, double*,
+                                           cudaStream_t);
+
+}  // namespace bd

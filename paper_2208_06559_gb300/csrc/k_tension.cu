@@ -1,0 +1,412 @@
+// k_tension.cu -- flow predictor, rod-tension solve and observables.
+//
+// Rigid rods are the K* -> infinity limit of the paper's semi-implicit
+// Fraenkel scheme (Sec. 3 Eqs. (13)-(17)): Eq. (17) gives |Q| = 1 and, rod by
+// rod, the tension (|Y| - 1) / (2 dt) that brings the predicted link vector Y
+// back to unit length.  That self-only tension is the starting point here;
+// the tensions of all rods are then found together so that every rod of
+// r(T) = r* + dt D F(T),  F_i = T_i u_i - T_{i-1} u_{i-1}
+// has unit length (u_k the rod directions at the start of the step).
+//
+// The residual is g_k = |Q_k(T)|^2 - 1.  Its Jacobian is
+// -2 dt diag(Q(T))^T C^T D C diag(u); the solver keeps its value at Q = u,
+// -2 dt K with K = U^T C^T D C U (symmetric positive definite, factored once
+// per step), and iterates T <- T + K^{-1} g / (2 dt) until max|g| <= tol,
+// followed by one more update, exactly the stopping rule of the oracle's
+// Newton.  The root is the same; the convergence is linear with a rate of
+// order |Q - u| ~ sqrt(dt) instead of quadratic.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "bd_internal.h"
+
+namespace bd {
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ predictor
+// r* = r + dt kappa.r + y; u_k = Q_k / |Q_k| at the old positions;
+// T0_k = (|Q*_k| - 1) / (2 dt); F0 = F(T0).  One thread per bead.
+__global__ void k_predictor(const double* __restrict__ r, const double* __restrict__ y,
+                            const ChainDesc* __restrict__ cd, int n_chains, Phys ph,
+                            double* __restrict__ rstar, double* __restrict__ uhat,
+                            double* __restrict__ T, double* __restrict__ F,
+                            int* __restrict__ state, const int* __restrict__ status,
+                            int* __restrict__ iters) {
+  const int c = blockIdx.y;
+  const ChainDesc d = cd[c];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    state[c] = (status[c] == BD_OK) ? NS_ACTIVE : NS_FAILED;
+    iters[c] = 0;
+  }
+  if (i >= d.N) return;
+  auto pred = [&](int b, double out[3]) {
+    const double* rb = r + 3 * (d.boff + b);
+    const double* yb = y + 3 * (d.boff + b);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double kr = ph.kappa[3 * k] * rb[0] + ph.kappa[3 * k + 1] * rb[1] + ph.kappa[3 * k + 2] * rb[2];
+      out[k] = rb[k] + ph.dt * kr + yb[k];
+    }
+  };
+  double ri[3];
+  pred(i, ri);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) rstar[3 * (d.boff + i) + k] = ri[k];
+  double ui[3] = {0, 0, 0}, Ti = 0.0;
+  if (i < d.m) {
+    double rn[3];
+    pred(i + 1, rn);
+    const double* a0 = r + 3 * (d.boff + i);
+    double q[3] = {a0[3] - a0[0], a0[4] - a0[1], a0[5] - a0[2]};
+    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    const double qs0 = rn[0] - ri[0], qs1 = rn[1] - ri[1], qs2 = rn[2] - ri[2];
+    Ti = (sqrt(qs0 * qs0 + qs1 * qs1 + qs2 * qs2) - 1.0) / (2.0 * ph.dt);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ui[k] = q[k] / qn;
+      uhat[3 * (d.roff + i) + k] = ui[k];
+    }
+    T[d.roff + i] = Ti;
+  }
+  // F_i = T_i u_i - T_{i-1} u_{i-1}: the previous rod's values are recomputed
+  double Fi[3] = {Ti * ui[0], Ti * ui[1], Ti * ui[2]};
+  if (i > 0) {
+    double rp[3];
+    pred(i - 1, rp);
+    const double* a0 = r + 3 * (d.boff + i - 1);
+    double q[3] = {a0[3] - a0[0], a0[4] - a0[1], a0[5] - a0[2]};
+    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    const double qs0 = ri[0] - rp[0], qs1 = ri[1] - rp[1], qs2 = ri[2] - rp[2];
+    const double Tp = (sqrt(qs0 * qs0 + qs1 * qs1 + qs2 * qs2) - 1.0) / (2.0 * ph.dt);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fi[k] -= Tp * (q[k] / qn);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F[3 * (d.boff + i) + k] = Fi[k];
+}
+
+cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd, int n_chains,
+                             int max_N, Phys ph, double* rstar, double* uhat, double* T, double* F,
+                             int* state, const int* status, int* iters, cudaStream_t s) {
+  k_predictor<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, y, cd, n_chains, ph, rstar,
+                                                                    uhat, T, F, state, status, iters);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- Newton residual
+// One CTA per chain: r(T) = r* + dt u (u = D F(T)), g_k, max|g|, state.
+__global__ void __launch_bounds__(256) k_newton_residual(const double* __restrict__ rstar,
+                                                         const double* __restrict__ u,
+                                                         const ChainDesc* __restrict__ cd, Phys ph,
+                                                         double* __restrict__ rT,
+                                                         double* __restrict__ rhs,
+                                                         int* __restrict__ state,
+                                                         int* __restrict__ status,
+                                                         const int* __restrict__ iters) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const int st = state[c];
+  if (st >= NS_DONE) return;
+  if (status[c] != BD_OK) {  // e.g. K not positive definite
+    if (threadIdx.x == 0) state[c] = NS_FAILED;
+    return;
+  }
+  const ChainDesc d = cd[c];
+  const long long b3 = 3 * d.boff;
+  for (int e = threadIdx.x; e < d.n; e += blockDim.x) rT[b3 + e] = rstar[b3 + e] + ph.dt * u[b3 + e];
+  __syncthreads();
+  double gmax = 0.0;
+  const double inv2dt = 0.5 / ph.dt;
+  for (int k = threadIdx.x; k < d.m; k += blockDim.x) {
+    const double* a = rT + b3 + 3 * k;
+    const double q0 = a[3] - a[0], q1 = a[4] - a[1], q2 = a[5] - a[2];
+    const double g = q0 * q0 + q1 * q1 + q2 * q2 - 1.0;
+    rhs[d.roff + k] = g * inv2dt;
+    gmax = (g != g) ? INFINITY : fmax(gmax, fabs(g));
+  }
+  gmax = block_max(gmax, red);
+  if (threadIdx.x == 0) {
+    int ns = st;
+    if (st == NS_EXTRA) {
+      ns = NS_DONE;
+    } else if (gmax <= ph.tol) {
+      ns = NS_EXTRA;
+    } else if (iters[c] >= ph.max_newton || !(gmax < INFINITY)) {
+      ns = NS_FAILED;
+      atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
+    }
+    state[c] = ns;
+  }
+}
+
+cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
+                                   int n_chains, Phys ph, double* rT, double* rhs, int* state,
+                                   int* status, const int* iters, cudaStream_t s) {
+  k_newton_residual<<<n_chains, 256, 0, s>>>(rstar, u, cd, ph, rT, rhs, state, status, iters);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Newton solve
+// One CTA per chain: K delta = rhs with K = L_K L_K^T (row-major lower factor
+// of order m, padded to mp), T += delta, iters++, then F(T) for the next
+// mobility product.  Forward sweep right-looking, backward sweep left-looking;
+// 32-row blocks, warps over rows and lanes over columns (coalesced).
+template <typename T>
+__global__ void __launch_bounds__(256) k_newton_solve(const T* __restrict__ K,
+                                                      const ChainDesc* __restrict__ cd, Phys ph,
+                                                      const double* __restrict__ uhat,
+                                                      double* __restrict__ rhs,
+                                                      double* __restrict__ Tn,
+                                                      double* __restrict__ F,
+                                                      int* __restrict__ state,
+                                                      int* __restrict__ iters) {
+  __shared__ double part[8][32];
+  const int c = blockIdx.x;
+  const int st = state[c];
+  if (st != NS_ACTIVE && st != NS_EXTRA) return;
+  const ChainDesc d = cd[c];
+  const int m = d.m;
+  const long long mp = d.mp;
+  const T* L = K + d.koff;
+  double* z = rhs + d.roff;  // solved in place
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = (m + 31) / 32;
+  // forward: L z = rhs
+  for (int b = 0; b < nb; ++b) {
+    const int r0 = 32 * b;
+    if (warp == 0) {
+      const int row = r0 + lane;
+      double s = (row < m) ? z[row] : 0.0;
+      for (int j = 0; j < 32; ++j) {
+        const int cj = r0 + j;
+        double zj = 0.0;
+        if (lane == j && row < m) zj = s / (double)L[row * mp + row];
+        zj = __shfl_sync(0xffffffffu, zj, j);
+        if (lane > j && row < m && cj < m) s -= (double)L[row * mp + cj] * zj;
+        if (lane == j) s = zj;
+      }
+      if (row < m) z[row] = s;
+    }
+    __syncthreads();
+    // rows below the block: z[row] -= L[row][r0..r0+31] . z[r0..]
+    const double zb = (r0 + lane < m) ? z[r0 + lane] : 0.0;
+    for (int row = r0 + 32 + warp; row < m; row += 8) {
+      double v = (r0 + lane < m) ? (double)L[row * mp + r0 + lane] * zb : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) z[row] -= v;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = z
+  for (int b = nb - 1; b >= 0; --b) {
+    const int c0 = 32 * b;
+    const int col = c0 + lane;
+    double acc = 0.0;
+    for (int row = c0 + 32 + warp; row < m; row += 8)
+      if (col < m) acc += (double)L[row * mp + col] * z[row];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      double s = (col < m) ? z[col] : 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s -= part[w][lane];
+      for (int j = 31; j >= 0; --j) {
+        const int cj = c0 + j;
+        double xj = 0.0;
+        if (lane == j && col < m) xj = s / (double)L[col * mp + col];
+        xj = __shfl_sync(0xffffffffu, xj, j);
+        if (lane < j && cj < m && col < m) s -= (double)L[cj * mp + col] * xj;
+        if (lane == j) s = xj;
+      }
+      if (col < m) z[col] = s;
+    }
+    __syncthreads();
+  }
+  // T += delta
+  for (int k = threadIdx.x; k < m; k += blockDim.x) Tn[d.roff + k] += z[k];
+  __syncthreads();
+  // F(T)
+  for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double f = 0.0;
+      if (i < m) f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
+      if (i > 0) f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
+      F[3 * (d.boff + i) + q] = f;
+    }
+  }
+  if (threadIdx.x == 0) iters[c] += 1;
+}
+
+template <typename T>
+cudaError_t launch_newton_solve(const T* K, const ChainDesc* cd, int n_chains, Phys ph,
+                                const double* uhat, double* rhs, double* Tn, double* F, int* state,
+                                int* iters, cudaStream_t s) {
+  k_newton_solve<T><<<n_chains, 256, 0, s>>>(K, cd, ph, uhat, rhs, Tn, F, state, iters);
+  return cudaGetLastError();
+}
+
+// Sets the while-node condition: 1 while any chain is ACTIVE or EXTRA and the
+// loop has run fewer than max_loops times in this step (a chain still active
+// then is failed by k_finalize; with the per-chain cap of max_newton updates
+// the bound is never reached by a correct state machine).
+__global__ void k_any_active(const int* __restrict__ state, int n_chains,
+                             cudaGraphConditionalHandle h, unsigned long long* loops,
+                             StepArgs* args, int max_loops) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < n_chains; c += blockDim.x)
+    if (state[c] == NS_ACTIVE || state[c] == NS_EXTRA) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int k = ++args->loops_in_step;
+    cudaGraphSetConditional(h, (any && k < max_loops) ? 1u : 0u);
+    *loops += 1;
+  }
+}
+
+cudaError_t launch_newton_any_active(const int* state, int n_chains, cudaGraphConditionalHandle h,
+                                     unsigned long long* loops, StepArgs* args, int max_loops,
+                                     cudaStream_t s) {
+  k_any_active<<<1, 256, 0, s>>>(state, n_chains, h, loops, args, max_loops);
+  return cudaGetLastError();
+}
+
+// Commit r <- r(T) for chains that converged; failed chains keep r.
+__global__ void k_finalize(const ChainDesc* __restrict__ cd, const double* __restrict__ rT,
+                           double* __restrict__ r, const int* __restrict__ state,
+                           int* __restrict__ status, StepArgs* args) {
+  const int c = blockIdx.y;
+  const ChainDesc d = cd[c];
+  const int st = state[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st != NS_DONE && st != NS_FAILED)
+    atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);  // loop ended early (not expected)
+  if (st == NS_DONE) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.n; e += gridDim.x * blockDim.x)
+      r[3 * d.boff + e] = rT[3 * d.boff + e];
+  }
+  if (args && c == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    args->step += 1;
+    args->loops_in_step = 0;
+  }
+}
+
+cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_beads,
+                            const double* rT, double* r, const int* state, int* status,
+                            StepArgs* args, cudaStream_t s) {
+  (void)total_beads;
+  k_finalize<<<dim3(4, n_chains), 256, 0, s>>>(cd, rT, r, state, status, args);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ observables
+// Sec. 5 Eqs. (25)-(27) per chain (ensemble averages are the caller's).
+__global__ void __launch_bounds__(256) k_observables(const double* __restrict__ r,
+                                                     const ChainDesc* __restrict__ cd,
+                                                     const int* __restrict__ iters,
+                                                     double* __restrict__ obs) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const ChainDesc d = cd[c];
+  const double* rc = r + 3 * d.boff;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+    s0 += rc[3 * i];
+    s1 += rc[3 * i + 1];
+    s2 += rc[3 * i + 2];
+  }
+  const double cx = block_sum(s0, red) / d.N, cy = block_sum(s1, red) / d.N,
+               cz = block_sum(s2, red) / d.N;
+  double g = 0.0, md = 0.0;
+  for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+    const double dx = rc[3 * i] - cx, dy = rc[3 * i + 1] - cy, dz = rc[3 * i + 2] - cz;
+    g += dx * dx + dy * dy + dz * dz;
+    if (i < d.m) {
+      const double q0 = rc[3 * i + 3] - rc[3 * i], q1 = rc[3 * i + 4] - rc[3 * i + 1],
+                   q2 = rc[3 * i + 5] - rc[3 * i + 2];
+      md = fmax(md, fabs(sqrt(q0 * q0 + q1 * q1 + q2 * q2) - 1.0));
+    }
+  }
+  const double rg2 = block_sum(g, red) / d.N;
+  md = block_max(md, red);
+  if (threadIdx.x == 0) {
+    const double* e = rc + 3 * (d.N - 1);
+    const double rx = e[0] - rc[0], ry = e[1] - rc[1], rz = e[2] - rc[2];
+    const double R2 = rx * rx + ry * ry + rz * rz;
+    double* o = obs + (long long)c * BD_OBS_STRIDE;
+    o[0] = rx;
+    o[1] = ry;
+    o[2] = rz;
+    o[3] = R2;
+    o[4] = rg2;
+    o[5] = sqrt(R2) / (d.N - 1);
+    o[6] = md;
+    o[7] = (double)iters[c];
+  }
+}
+
+cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chains,
+                               const int* iters, double* obs, cudaStream_t s) {
+  k_observables<<<n_chains, 256, 0, s>>>(r, cd, iters, obs);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_args(StepArgs* args, const double* noise, long long stride) {
+  args->noise = noise;
+  args->stride = stride;
+  args->step = 0;
+  args->loops_in_step = 0;
+}
+
+cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
+                            cudaStream_t s) {
+  k_set_args<<<1, 1, 0, s>>>(args, noise, stride);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_newton_solve<double>(const double*, const ChainDesc*, int, Phys,
+                                                 const double*, double*, double*, double*, int*,
+                                                 int*, cudaStream_t);
+template cudaError_t launch_newton_solve<float>(const float*, const ChainDesc*, int, Phys,
+                                                const double*, double*, double*, double*, int*,
+                                                int*, cudaStream_t);
+
+}  // namespace bd
