@@ -157,6 +157,29 @@ int bd_get_tensions(bd_ctx* ctx, double* T_dev, void* stream);
  * diagonal).  Synchronises the legacy default stream. */
 int bd_read_matrix(bd_ctx* ctx, int chain, int which, double* out_host);
 
+/* ---- allocation-free entry point ----
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory (code inside a host framework that owns all device
+ * allocations, or a thread that must not call cudaMalloc/cudaFree, which can
+ * synchronise the device) and therefore cannot create a bd_ctx.
+ *
+ * u = D(r) f for ONE chain of n_beads <= BD_STATIC_MAX_BEADS beads, with D the
+ * RPY diffusion tensor of Sec. 3 Eqs. (7)-(9) evaluated on the fly from the
+ * positions (h_star >= 0; a <= 0 means a = h_star; a < h_star is rejected).
+ * r_dev, f_dev, u_dev: device FP64 [n_beads][3], owned by the caller.
+ * It allocates nothing: its scratch is a fixed file-scope device array of
+ * 786,432 bytes that every GPU loading the library holds until exit.  The
+ * first call on each device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the array and writes each slot before reading
+ * it, so calls whose work overlaps on the GPU (other streams or host threads)
+ * race and must be serialised by the caller.  Asynchronous on `stream`.
+ * Errors: BD_ERR_ARG (NULL pointer, n_beads < 1 or > BD_STATIC_MAX_BEADS, bad
+ * h_star/a), BD_ERR_CUDA. */
+#define BD_STATIC_MAX_BEADS 1024
+int bd_mobility_apply_static(const double* r_dev, int n_beads, double h_star, double a,
+                             const double* f_dev, double* u_dev, void* stream);
+
 /* Human-readable text for an error code (static storage). */
 const char* bd_strerror(int code);
 

@@ -75,7 +75,11 @@ EXPORTS = {
     "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bd_kernel_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.c_void_p]),
+    "bd_mobility_apply_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
 }
+STATIC_MAX_BEADS = 1024
 
 
 def lib():
@@ -116,6 +120,18 @@ def _stream(stream) -> ctypes.c_void_p:
 
 def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
+
+
+def mobility_apply_static(r, f, h_star: float = 0.25, a: float = 0.0, out=None, stream=None):
+    """u = D(r) f for one chain through the allocation-free entry point
+    (positions r and forces f: CUDA float64 [N, 3], N <= STATIC_MAX_BEADS)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(f)
+    _check(lib().bd_mobility_apply_static(_ptr(r), int(r.shape[0]), float(h_star), float(a),
+                                          _ptr(f), _ptr(out), _stream(stream)),
+           "bd_mobility_apply_static")
+    return out
 
 
 class Context:
