@@ -12,6 +12,7 @@
 //     32) for the rod-coupling matrix K = U^T C^T D C U and its factor;
 //   * FP64 (BD_FP64) or FP32 (mixed) element type for both matrices.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,12 +27,14 @@ struct ChainDesc {
   int np;          // padded order of the D/L matrix
   int m;           // rods N-1
   int mp;          // padded order of K
-  int pad_;
+  int wrow;        // mixed: first row of this chain's diagonal-tile inverses in Winv
   long long boff;  // first bead in packed [sum N][3] arrays
   long long roff;  // first rod in packed [sum (N-1)] arrays
   long long moff;  // first element of the D/L matrix
   long long koff;  // first element of K
   long long soff;  // first element of the SYMV partial-sum scratch
+  long long swrow; // FP64 path: first row of this chain's 32 x 32 diagonal-block inverses of L
+  long long kwrow; // first row of this chain's 32 x 32 diagonal-block inverses of K's factor
 };
 
 enum NewtonState : int { NS_ACTIVE = 0, NS_EXTRA = 1, NS_DONE = 2, NS_FAILED = 3 };
@@ -68,7 +71,7 @@ template <typename T>
 cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_chains,
                             int max_N, double hstar, double a, cudaStream_t s);
 template <typename T>
-cudaError_t launch_chol_simt(T* M, const ChainDesc* cd, int n_chains, int max_tiles,
+cudaError_t launch_chol_simt(T* M, T* Winv, const ChainDesc* cd, int n_chains, int max_tiles,
                              bool k_matrix, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trmv(const T* M, const ChainDesc* cd, int n_chains, int max_n,
@@ -91,7 +94,7 @@ cudaError_t launch_newton_residual(const double* rstar, const double* u, const C
                                    int* state, int* status, const int* iters,
                                    cudaStream_t s);
 template <typename T>
-cudaError_t launch_newton_solve(const T* K, const ChainDesc* cd, int n_chains, Phys ph,
+cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F,
                                 int* state, int* iters, cudaStream_t s);
 cudaError_t launch_newton_any_active(const int* state, int n_chains,
@@ -104,6 +107,26 @@ cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chain
                                const int* iters, double* obs, cudaStream_t s);
 cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
                             cudaStream_t s);
+// Opt-in shared-memory sizes of the matvec kernels (once per device).
+cudaError_t matvec_configure();
+cudaError_t tension_configure();
+
+// Mixed-precision Brownian displacement with one refinement step (k_refine.cu):
+// y = s/2 (B xi + D B^{-T} xi); with refine == 0, y = s B xi.
+cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
+                                int max_np, const double* x, const StepArgs* args, double scale,
+                                bool refine, double* y, double* y1, double* z, double* w,
+                                double* scratch, cudaStream_t s);
+
+// Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
+bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains);
+cudaError_t tc_configure();
+// Factor chains [0, n_chains) of the given arrays (pointers may be offset to
+// a chain subrange); wmap is the TMA map of Winv.
+cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
+                           const ChainDesc* cd, int n_chains, int max_tiles, int* status,
+                           cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_extract(const T* M, const ChainDesc* cd, int chain, int which, double* out,
                            cudaStream_t s);

@@ -12,6 +12,7 @@
 // the same graph serves every call.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -41,6 +42,10 @@ struct bd_ctx {
   size_t elem = 8;
   double *r = nullptr, *rstar = nullptr, *rT = nullptr, *y = nullptr, *u = nullptr, *F = nullptr;
   double *uhat = nullptr, *T = nullptr, *rhs = nullptr, *scratch = nullptr, *obs = nullptr;
+  float* Winv = nullptr;           // mixed: inverses of the diagonal tiles, [sum np][128]
+  void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
+  void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
+  CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
   double* stage = nullptr;  // staging for host-memory noise / observables
   size_t stage_elems = 0;
   int *status = nullptr, *state = nullptr, *iters = nullptr;
@@ -49,9 +54,18 @@ struct bd_ctx {
   unsigned long long steps_launched = 0;
   size_t graph_kernels = 0, body_kernels = 0;
   cudaStream_t cs = nullptr, cs2 = nullptr;
+  // mixed factorisation: chain groups on their own streams, so that one
+  // group's latency-bound diagonal-tile step overlaps another's products
+  static constexpr int kMaxGroups = 4;
+  int n_groups = 1;
+  std::vector<int> group_start;      // chain index of each group's first chain (+ end)
+  std::vector<int> group_tiles;      // max 128-tiles of each group
+  cudaStream_t gs[kMaxGroups] = {};
+  cudaEvent_t gev[kMaxGroups + 1] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool have_state = false;
+  int direct_iters = 0;  // > 0: launch the step's kernels directly (profiling), no graph
   std::mutex mu;
 };
 
@@ -78,11 +92,29 @@ struct DeviceGuard {
     }                                                                             \
   } while (0)
 
-template <typename T>
-int enqueue_factor_t(bd_ctx* c, cudaStream_t s) {
-  T* M = static_cast<T*>(c->M);
-  // Tensor-core path for mixed precision is selected in chol_dispatch.
-  CK(launch_chol_simt<T>(M, c->d_cd, c->n_chains, c->max_np / kSimtTile, false, c->status, s));
+int enqueue_factor(bd_ctx* c, cudaStream_t s) {
+  if (c->mixed) {
+    const CUtensorMap* wmap = c->tmaps + c->n_chains;
+    if (c->n_groups <= 1) {
+      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps, wmap, c->d_cd, c->n_chains,
+                        c->max_np / kMixedTile, c->status, s));
+      return BD_OK;
+    }
+    // fork
+    CK(cudaEventRecord(c->gev[c->kMaxGroups], s));
+    for (int g = 0; g < c->n_groups; ++g) {
+      CK(cudaStreamWaitEvent(c->gs[g], c->gev[c->kMaxGroups], 0));
+      const int c0 = c->group_start[g], c1 = c->group_start[g + 1];
+      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps + c0, wmap, c->d_cd + c0, c1 - c0,
+                        c->group_tiles[g], c->status + c0, c->gs[g]));
+      CK(cudaEventRecord(c->gev[g], c->gs[g]));
+    }
+    // join
+    for (int g = 0; g < c->n_groups; ++g) CK(cudaStreamWaitEvent(s, c->gev[g], 0));
+    return BD_OK;
+  }
+    CK(launch_chol_simt<double>((double*)c->M, (double*)c->Minv, c->d_cd, c->n_chains,
+                                c->max_np / kSimtTile, false, c->status, s));
   return BD_OK;
 }
 
@@ -95,16 +127,14 @@ int enqueue_assemble(bd_ctx* c, cudaStream_t s) {
   return BD_OK;
 }
 
-int enqueue_factor(bd_ctx* c, cudaStream_t s) {
-  return c->mixed ? enqueue_factor_t<float>(c, s) : enqueue_factor_t<double>(c, s);
-}
 
 // y = sqrt(2 dt) B xi; xi from `x` or, when args != NULL, from the step's
 // slice of the noise array.
 int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y, cudaStream_t s) {
   const double sc = c->ph.sq2dt;
-  if (c->mixed)
-    CK(launch_trmv<float>((const float*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
+  if (c->mixed)  // buffers rT, F, u are free at this point of the step
+    CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, x, args, sc,
+                           c->p.refine != 0, y, c->rT, c->F, c->u, c->scratch, s));
   else
     CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
   return BD_OK;
@@ -130,13 +160,13 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   if (c->mixed) {
     CK(launch_form_k<float>((const float*)c->M, (float*)c->K, c->d_cd, c->n_chains, c->max_m,
                             c->uhat, s));
-    CK(launch_chol_simt<float>((float*)c->K, c->d_cd, c->n_chains, c->max_mp / kSimtTile, true,
-                               c->status, s));
+    CK(launch_chol_simt<float>((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains,
+                               c->max_mp / kSimtTile, true, c->status, s));
   } else {
     CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
                              c->uhat, s));
-    CK(launch_chol_simt<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp / kSimtTile, true,
-                                c->status, s));
+    CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
+                                c->max_mp / kSimtTile, true, c->status, s));
   }
   return BD_OK;
 }
@@ -147,10 +177,10 @@ int enqueue_newton_body(bd_ctx* c, cudaGraphConditionalHandle h, cudaStream_t s)
   CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
                             c->status, c->iters, s));
   if (c->mixed)
-    CK(launch_newton_solve<float>((const float*)c->K, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
+    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
                                   c->T, c->F, c->state, c->iters, s));
   else
-    CK(launch_newton_solve<double>((const double*)c->K, c->d_cd, c->n_chains, c->ph, c->uhat,
+    CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat,
                                    c->rhs, c->T, c->F, c->state, c->iters, s));
   CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->ph.max_newton + 3, s));
   return BD_OK;
@@ -216,6 +246,28 @@ int build_step_graph(bd_ctx* c) {
   c->graph_kernels = count_kernel_nodes(g);
   c->body_kernels = count_kernel_nodes(body);
   CK(cudaGraphInstantiate(&c->exec, g, 0));
+  return BD_OK;
+}
+
+// Direct (graph-free) step for kernel-level profilers that cannot see into a
+// graph's conditional node: the same kernels, with the tension-solve body
+// enqueued a fixed number of times (converged chains skip it on the device).
+int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
+  int rc;
+  if ((rc = enqueue_pre_newton(c, s))) return rc;
+  for (int it = 0; it < c->direct_iters; ++it) {
+    if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+    CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
+                              c->status, c->iters, s));
+    if (c->mixed)
+      CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
+                                    c->T, c->F, c->state, c->iters, s));
+    else
+      CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat,
+                                     c->rhs, c->T, c->F, c->state, c->iters, s));
+  }
+  CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
+                     c->args, s));
   return BD_OK;
 }
 
@@ -321,9 +373,14 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->args, c->loops};
+                  c->stage, c->status, c->state, c->iters, c->args, c->loops, c->Winv, c->tmaps,
+                  c->Minv, c->Kinv};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
+    if (c->gs[g]) cudaStreamDestroy(c->gs[g]);
+  for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
+    if (c->gev[g]) cudaEventDestroy(c->gev[g]);
   if (c->cs) cudaStreamDestroy(c->cs);
   if (c->cs2) cudaStreamDestroy(c->cs2);
   delete c;
@@ -339,8 +396,11 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (p->flow < BD_FLOW_NONE || p->flow > BD_FLOW_UNIAXIAL) return BD_ERR_ARG;
   if (p->precision < BD_FP64 || p->precision > BD_MIXED_BF16) return BD_ERR_ARG;
   if (p->constraint != BD_RIGID) return BD_ERR_ARG;
+  // limits of the per-chain kernels: the tension solve holds N - 1 <= 4096
+  // unknowns in shared memory; the refinement's triangular solve owns up to
+  // 12 columns per thread of a 1024-thread block (3N <= 12288 after padding)
   for (int i = 0; i < p->n_chains; ++i)
-    if (p->n_beads[i] < 2 || p->n_beads[i] > (1 << 20)) return BD_ERR_ARG;
+    if (p->n_beads[i] < 2 || p->n_beads[i] > 4096) return BD_ERR_ARG;
 
   bd_ctx* c = new (std::nothrow) bd_ctx();
   if (!c) return BD_ERR_OOM;
@@ -370,8 +430,12 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   ph.tol = p->tol > 0.0 ? p->tol : 1e-13;
   ph.max_newton = p->max_newton > 0 ? p->max_newton : 50;
   ph.n_chains = c->n_chains;
+  if (const char* e = getenv("BD_STEP_DIRECT")) {
+    const int v = atoi(e);
+    c->direct_iters = v > 0 ? (v == 1 ? ph.max_newton + 2 : v) : 0;
+  }
 
-  long long boff = 0, roff = 0, moff = 0, koff = 0, soff = 0;
+  long long boff = 0, roff = 0, moff = 0, koff = 0, soff = 0, wrow = 0, swrow = 0, kwrow = 0;
   c->h_cd.resize(c->n_chains);
   for (int i = 0; i < c->n_chains; ++i) {
     ChainDesc& d = c->h_cd[i];
@@ -386,12 +450,21 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     d.moff = moff;
     d.koff = koff;
     d.soff = soff;
-    const long long tsn = ceil_div(d.n, kSymvTile);
+    d.wrow = (int)wrow;
+    d.swrow = swrow;
+    d.kwrow = kwrow;
+    const long long tsn = ceil_div(d.n, kSymvTile), tsn2 = ceil_div(d.n, 2 * kSymvTile);
+    const long long sneed = tsn * tsn * kSymvTile > tsn2 * tsn2 * 2 * kSymvTile
+                                ? tsn * tsn * kSymvTile
+                                : tsn2 * tsn2 * 2 * kSymvTile;
     boff += d.N;
     roff += d.m;
     moff += (long long)d.np * d.np;
     koff += (long long)d.mp * d.mp;
-    soff += tsn * tsn * kSymvTile;
+    soff += sneed;
+    wrow += d.np;
+    swrow += d.np;
+    kwrow += d.mp;
     c->max_N = d.N > c->max_N ? d.N : c->max_N;
     c->max_n = d.n > c->max_n ? d.n : c->max_n;
     c->max_np = d.np > c->max_np ? d.np : c->max_np;
@@ -424,6 +497,11 @@ int bd_create(const bd_params* p, bd_ctx** out) {
             alloc((void**)&c->iters, sizeof(int) * c->n_chains) &&
             alloc((void**)&c->args, sizeof(StepArgs)) &&
             alloc((void**)&c->loops, sizeof(unsigned long long));
+  ok = ok && alloc(&c->Kinv, (size_t)kwrow * kSimtTile * c->elem) &&
+       (c->mixed || alloc(&c->Minv, (size_t)swrow * kSimtTile * c->elem));
+  if (ok && c->mixed)
+    ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
+         alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
     return BD_ERR_OOM;
@@ -436,6 +514,35 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess)
     return fail(BD_ERR_CUDA);
   cudaStream_t s = c->cs;
+  if (c->mixed) {
+    c->n_groups = c->n_chains / 16;
+    if (c->n_groups < 1) c->n_groups = 1;
+    if (c->n_groups > bd_ctx::kMaxGroups) c->n_groups = bd_ctx::kMaxGroups;
+    c->group_start.assign(c->n_groups + 1, 0);
+    c->group_tiles.assign(c->n_groups, 0);
+    for (int g = 0; g <= c->n_groups; ++g)
+      c->group_start[g] = (int)((long long)c->n_chains * g / c->n_groups);
+    for (int g = 0; g < c->n_groups; ++g)
+      for (int i = c->group_start[g]; i < c->group_start[g + 1]; ++i)
+        if (c->h_cd[i].np / kMixedTile > c->group_tiles[g]) c->group_tiles[g] = c->h_cd[i].np / kMixedTile;
+    if (c->n_groups > 1) {
+      for (int g = 0; g < c->n_groups; ++g)
+        if (cudaStreamCreateWithFlags(&c->gs[g], cudaStreamNonBlocking) != cudaSuccess)
+          return fail(BD_ERR_CUDA);
+      for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
+        if (cudaEventCreateWithFlags(&c->gev[g], cudaEventDisableTiming) != cudaSuccess)
+          return fail(BD_ERR_CUDA);
+    }
+    std::vector<CUtensorMap> hm(c->n_chains + 1);
+    if (!make_tc_maps(hm.data(), (float*)c->M, c->Winv, c->h_cd.data(), c->n_chains))
+      return fail(BD_ERR_CUDA);
+    if (cudaMemcpy(c->tmaps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        tc_configure() != cudaSuccess)
+      return fail(BD_ERR_CUDA);
+  }
+  if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess)
+    return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(c->M, 0, c->M_elems * c->elem, s) != cudaSuccess ||
@@ -488,7 +595,7 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = build_step_graph(c);
+  int rc = c->direct_iters > 0 ? BD_OK : build_step_graph(c);
   if (rc) return rc;
   const long long stride = c->total_beads * 3;
   const double* nz = noise;
@@ -499,6 +606,11 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
     nz = c->stage;
   }
   CK(launch_set_args(c->args, nz, stride, s));
+  if (c->direct_iters > 0) {
+    for (int i = 0; i < n_steps; ++i)
+      if ((rc = enqueue_step_direct(c, s))) return rc;
+    return BD_OK;
+  }
   for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, s));
   c->steps_launched += (unsigned long long)n_steps;
   return BD_OK;

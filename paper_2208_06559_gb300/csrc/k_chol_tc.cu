@@ -1,0 +1,465 @@
+// k_chol_tc.cu -- mixed-precision blocked Cholesky on the tensor cores
+// (Sec. 3 Eq. (10)), the dominant cost of the step (89 % of the paper's step
+// time, Sec. 4 Table 1).
+//
+// The paper calls cuSOLVER dpotrf in FP64 (its Tables 2-3 profile the
+// library's internal trsm and dgemm kernels).  Here the matrix of every chain
+// is FP32, row-major, padded to a multiple of 128, and for each 128-wide
+// block column k three launches cover the whole batch:
+//
+//   potrf128 : factor the 128 x 128 diagonal tile on the CUDA cores (FP32)
+//              and form its inverse W = L_kk^{-1} so that the panel solve
+//              becomes a product.
+//   tc_gemm<TRSM>   : L_ik = A_ik W^T for every tile below the diagonal.
+//   tc_gemm<UPDATE> : A_ij -= sum_{k0<=k<k1} L_ik L_jk^T for the trailing
+//              lower tiles (diagonal tiles: lower triangle only).
+//
+// The two products run on the 5th-generation tensor cores: TMA loads 128 x 32
+// FP32 slices of both operands (128-byte swizzle) into a 2-stage shared-memory
+// ring guarded by mbarriers (three CTAs per SM overlap each other's epilogues), one thread issues tcgen05.mma kind::tf32
+// (128 x 128 x 8) accumulating in TMEM, the four warps read TMEM back with
+// tcgen05.ld, stage the tile in shared memory in the same swizzled layout, and
+// one TMA reduce-add (update) or store (panel solve) writes it to the matrix.
+// Operands are TF32 (10-bit mantissa), accumulation FP32.  No multicast.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdio.h>
+
+#include "bd_internal.h"
+#include "tc_ptx.h"
+
+namespace bd {
+
+using namespace tc;
+
+constexpr int NB = kMixedTile;             // 128
+constexpr int kStages = 2;  // 2 x 32 KiB ring: three CTAs share an SM
+constexpr int kChunkBytes = NB * 32 * 4;   // 128 rows x 32 fp32 = 16 KiB
+constexpr int kStageBytes = 2 * kChunkBytes;
+constexpr int kTcSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+enum TcMode { TC_UPDATE = 0, TC_TRSM = 1 };
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+// Output tile of this CTA.  UPDATE: tiles (i, j) with j in [j0, j1) and
+// i in [j, T), enumerated column by column.  TRSM: tiles (i, k0), i in (k0, T).
+__device__ __forceinline__ bool tile_of(int mode, int p, int T, int k0, int j0, int j1, int& i,
+                                        int& j) {
+  if (mode == TC_TRSM) {
+    i = k0 + 1 + p;
+    j = k0;
+    return i < T;
+  }
+  const int jend = j1 < T ? j1 : T;
+  for (j = j0; j < jend; ++j) {
+    const int cnt = T - j;
+    if (p < cnt) {
+      i = j + p;
+      return true;
+    }
+    p -= cnt;
+  }
+  return false;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restrict__ maps,
+                                                    const CUtensorMap* __restrict__ wmap,
+                                                    const ChainDesc* __restrict__ cd, int k0, int k1,
+                                                    int j0, int j1, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* fail = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int c = blockIdx.y;
+  const ChainDesc d = cd[c];
+  const int T = d.np / NB;
+  int ti, tj;
+  if (!tile_of(MODE, blockIdx.x, T, k0, j0, j1, ti, tj)) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *fail = 0;
+    fence_barrier_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(tmem_slot, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const CUtensorMap* am = maps + c;
+  const CUtensorMap* bm = (MODE == TC_TRSM) ? wmap : maps + c;
+  const int nchunks = (MODE == TC_TRSM) ? 4 : 4 * (k1 - k0);
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    prefetch_tmap(am);
+    if (MODE == TC_TRSM) prefetch_tmap(bm);
+    for (int q = 0; q < nchunks; ++q) {
+      const int s = q % kStages, round = q / kStages;
+      if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+        atomicExch(fail, 1);
+        break;
+      }
+      uint8_t* sa = smem + s * kStageBytes;
+      uint8_t* sb = sa + kChunkBytes;
+      mbar_arrive_expect_tx(&full[s], kStageBytes);
+      const int kx = k0 * NB + 32 * q;  // column of the K slice in the matrix
+      tma_load_2d(sa, am, &full[s], kx, ti * NB);
+      if (MODE == TC_TRSM)
+        tma_load_2d(sb, bm, &full[s], 32 * q, d.wrow + k0 * NB);
+      else
+        tma_load_2d(sb, bm, &full[s], kx, tj * NB);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = idesc_mma(2u /*tf32*/, 128u, 128u);
+    bool ok = true;
+    for (int q = 0; q < nchunks; ++q) {
+      const int s = q % kStages, round = q / kStages;
+      if (!mbar_wait(&full[s], round & 1)) {
+        atomicExch(fail, 1);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + s * kStageBytes);
+      const uint64_t ad = desc_sw128(sa), bdsc = desc_sw128(sa + kChunkBytes);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)  // K = 8 tf32 per MMA = 32 bytes of the 128-byte row
+        mma_tf32(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(done);
+  }
+  __syncwarp();
+
+  // ---- epilogue (all four warps; warp w owns TMEM lanes / tile rows 32w..)
+  const bool got = mbar_wait(done, 0);
+  __syncwarp();
+  tc_fence_after();
+  float* stage_out = reinterpret_cast<float*>(smem);  // 4 chunks x 16 KiB, reusing stages 0-1
+  const int row = threadIdx.x;
+  const bool diag = (MODE == TC_UPDATE) && (ti == tj);
+  if (got) {
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v[32];
+      tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32), v);
+      tmem_ld_wait();
+      float* chunk = stage_out + q * (kChunkBytes / 4) + row * 32;
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        float4 f;
+        float* fp = reinterpret_cast<float*>(&f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int col = 32 * q + 4 * j4 + e;
+          float val = __uint_as_float(v[4 * j4 + e]);
+          if (MODE == TC_UPDATE) {
+            val = -val;
+            if (diag && col > row) val = 0.0f;
+          }
+          fp[e] = val;
+        }
+        *reinterpret_cast<float4*>(chunk + 4 * (j4 ^ (row & 7))) = f;
+      }
+    }
+  } else {
+    atomicExch(fail, 1);
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*fail == 0) {
+      for (int q = 0; q < 4; ++q) {
+        const float* src = stage_out + q * (kChunkBytes / 4);
+        if (MODE == TC_UPDATE)
+          tma_reduce_add_2d(am, src, tj * NB + 32 * q, ti * NB);
+        else
+          tma_store_2d(am, src, k0 * NB + 32 * q, ti * NB);
+      }
+      bulk_commit();
+      bulk_wait_all();
+    } else {
+      atomicCAS(status + c, BD_OK, BD_ERR_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 128);
+  }
+}
+
+// ------------------------------------------------------------ potrf128
+// One CTA (512 threads) per chain factors the 128 x 128 diagonal tile k in
+// place and writes W = L_kk^{-1} (lower, zeros above) to rows
+// wrow + 128 k .. of Winv (kept for the refinement's triangular solve).
+// Recursive halving 128 -> 64 -> 32 -> 16: for a block [[A11, .], [A21, A22]]
+//   factor A11 -> L11, W11;  L21 = A21 W11^T;  A22 -= L21 L21^T;
+//   factor A22 -> L22, W22;  W21 = -W22 (L21 W11);
+// every product is split evenly over the 512 threads with register blocking;
+// the 16 x 16 leaves are factored by one warp in registers (lane r holds row
+// r, pivots broadcast by shuffles) together with their inverses.  All in
+// FP32: on this part FP64 issues at 1/64 of the FP32 rate, and the FP32
+// rounding of this tile (~1e-7 relative) is far below the TF32 rounding of
+// the products around it.
+constexpr int LDA = NB + 1;
+constexpr int SB = 16;
+constexpr int kPotrfThreads = 512;
+constexpr int kPotrfSmem = 3 * NB * LDA * 4 + 64;
+
+// 16 x 16 leaf at offset o: L (into A) and W_oo (into W), one warp, lane r
+// holding row r; pivots and rows are broadcast with shuffles.
+__device__ __forceinline__ void leaf16(float* A, float* W, int o, int* bad) {
+  const int lane = threadIdx.x & 31;
+  if ((threadIdx.x >> 5) == 0) {
+    const int r = lane & (SB - 1);
+    float a[SB];
+#pragma unroll
+    for (int q = 0; q < SB; ++q) a[q] = (q <= r) ? A[(o + r) * LDA + o + q] : 0.0f;
+    bool badl = false;
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+      const float djj = __shfl_sync(0xffffffffu, a[j], j);
+      const bool ok = djj > 0.0f;
+      badl |= !ok;
+      const float inv = rsqrtf(ok ? djj : 1.0f);
+      if (r == j) a[j] = (ok ? djj : 1.0f) * inv;
+      else if (r > j) a[j] *= inv;
+#pragma unroll
+      for (int q = j + 1; q < SB; ++q) {
+        const float lq = __shfl_sync(0xffffffffu, a[j], q);
+        if (r >= q) a[q] -= a[j] * lq;
+      }
+    }
+    float w[SB];
+#pragma unroll
+    for (int i = 0; i < SB; ++i) {
+      float sacc = (i == r) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int m = 0; m < i; ++m) sacc -= __shfl_sync(0xffffffffu, a[m], i) * w[m];
+      const float lii = __shfl_sync(0xffffffffu, a[i], i);
+      w[i] = (i >= r) ? sacc / lii : 0.0f;
+    }
+    if (lane < SB) {
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        if (q <= r) A[(o + r) * LDA + o + q] = a[q];
+        W[(o + q) * LDA + o + lane] = w[q];
+      }
+    }
+    if (__any_sync(0xffffffffu, badl && lane < SB) && lane == 0) *bad = 1;
+  }
+  __syncthreads();
+}
+
+// C (H x H, at rows rc, cols cc of buffer Cb) op= X * Y with
+//   TRANS_Y: Y element (m, c) read as Yb[(ry + c) * LDA + cy + m]  (Y^T stored)
+//   else   : Y element (m, c) read as Yb[(ry + m) * LDA + cy + c]
+// and X element (r, m) = Xb[(rx + r) * LDA + cx + m].  MODE 0: C = acc,
+// 1: C -= acc (lower triangle only when LOWER), 2: C = -acc.  Thread blocks
+// of RB x CB outputs; results are held in registers until every thread has
+// finished reading, so C may alias an input.
+template <int H, bool TRANS_Y, int MODE, bool LOWER>
+__device__ __forceinline__ void tile_gemm(float* Cb, int rc, int cc, const float* Xb, int rx, int cx,
+                                          const float* Yb, int ry, int cy) {
+  constexpr int OUT = H * H;
+  constexpr int PER = OUT / kPotrfThreads > 0 ? OUT / kPotrfThreads : 1;  // outputs per thread
+  constexpr int RB = PER >= 8 ? 4 : (PER >= 2 ? 2 : 1);
+  constexpr int CB = PER / RB > 0 ? PER / RB : 1;
+  constexpr int NCB = H / CB;       // column blocks
+  constexpr int NT = (H / RB) * NCB;  // threads used
+  float acc[RB][CB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int j = 0; j < CB; ++j) acc[i][j] = 0.0f;
+  const int t = threadIdx.x;
+  const bool active = t < NT;
+  const int r0 = (t / NCB) * RB, c0 = (t % NCB) * CB;
+  if (active) {
+#pragma unroll 4
+    for (int m = 0; m < H; ++m) {
+      float xv[RB], yv[CB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) xv[i] = Xb[(rx + r0 + i) * LDA + cx + m];
+#pragma unroll
+      for (int j = 0; j < CB; ++j)
+        yv[j] = TRANS_Y ? Yb[(ry + c0 + j) * LDA + cy + m] : Yb[(ry + m) * LDA + cy + c0 + j];
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) acc[i][j] += xv[i] * yv[j];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < CB; ++j) {
+        float* cp = Cb + (rc + r0 + i) * LDA + cc + c0 + j;
+        if (MODE == 0) *cp = acc[i][j];
+        else if (MODE == 2) *cp = -acc[i][j];
+        else if (!LOWER || c0 + j <= r0 + i) *cp -= acc[i][j];
+      }
+  }
+  __syncthreads();
+}
+
+template <int H>
+__device__ void potrf_rec(float* A, float* W, float* Tm, int o, int* bad) {
+  if constexpr (H == SB) {
+    leaf16(A, W, o, bad);
+  } else {
+    constexpr int h = H / 2;
+    const int o2 = o + h;
+    potrf_rec<h>(A, W, Tm, o, bad);
+    // L21 = A21 W11^T  (in place over A21)
+    tile_gemm<h, true, 0, false>(A, o2, o, A, o2, o, W, o, o);
+    // A22 -= L21 L21^T (lower)
+    tile_gemm<h, true, 1, true>(A, o2, o2, A, o2, o, A, o2, o);
+    potrf_rec<h>(A, W, Tm, o2, bad);
+    // Tm = L21 W11 ;  W21 = -W22 Tm
+    tile_gemm<h, false, 0, false>(Tm, o2, o, A, o2, o, W, o, o);
+    tile_gemm<h, false, 2, false>(W, o2, o, W, o2, o2, Tm, o2, o);
+  }
+}
+
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf128(float* __restrict__ M,
+                                                            float* __restrict__ Winv,
+                                                            const ChainDesc* __restrict__ cd, int k,
+                                                            int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  float* A = reinterpret_cast<float*>(smem_raw);  // [128][129] tile, then L
+  float* W = A + NB * LDA;                         // [128][129] inverse
+  float* Tm = W + NB * LDA;                        // [128][129] scratch
+  int* bad = reinterpret_cast<int*>(Tm + NB * LDA);
+  const int c = blockIdx.x;
+  const ChainDesc d = cd[c];
+  if (k * NB >= d.np) return;
+  float* base = M + d.moff + (long long)(k * NB) * d.np + k * NB;
+  const long long np = d.np;
+  const int tid = threadIdx.x;
+  if (tid == 0) *bad = 0;
+  for (int e = tid; e < NB * NB; e += kPotrfThreads) {
+    const int r = e >> 7, cc = e & 127;
+    A[r * LDA + cc] = (cc <= r) ? base[r * np + cc] : 0.0f;
+    W[r * LDA + cc] = 0.0f;
+  }
+  __syncthreads();
+  potrf_rec<NB>(A, W, Tm, 0, bad);
+  // write back L_kk (lower) and W (full tile, zeros above the diagonal)
+  float* wout = Winv + ((long long)d.wrow + (long long)k * NB) * NB;
+  for (int e = tid; e < NB * NB; e += kPotrfThreads) {
+    const int r = e >> 7, cc = e & 127;
+    if (cc <= r) base[r * np + cc] = A[r * LDA + cc];
+    wout[e] = W[r * LDA + cc];
+  }
+  if (tid == 0 && *bad) atomicCAS(status + c, BD_OK, BD_ERR_NOT_PD);
+}
+
+// ------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// FP32 row-major [rows][cols] matrix, 32 x 128 boxes, 128-byte swizzle.
+static bool encode_f32(CUtensorMap* out, void* base, uint64_t cols, uint64_t rows, uint64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)NB};
+  cuuint32_t es[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Fills maps[0..n_chains) (one per chain's matrix) and maps[n_chains] (Winv,
+// [sum_c np_c][128]).
+bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains) {
+  uint64_t wrows = 0;
+  for (int c = 0; c < n_chains; ++c) {
+    if (!encode_f32(&host_maps[c], M + h_cd[c].moff, h_cd[c].np, h_cd[c].np, h_cd[c].np)) return false;
+    wrows += h_cd[c].np;
+  }
+  return encode_f32(&host_maps[n_chains], Winv, NB, wrows, NB);
+}
+
+cudaError_t tc_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<TC_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_gemm<TC_TRSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_potrf128, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem);
+  return e;
+}
+
+// Right-looking with super-panels of kPanel tile columns: inside a panel,
+// column k first receives the updates of the panel's earlier columns
+// (K = 128 (k - K0)), is factored and solved; the trailing matrix is updated
+// once per panel with K = 128 kPanel, so every trailing tile is read and
+// written kPanel times less often than with single-column steps.
+constexpr int kPanel = 4;
+
+static int update_tiles(int T, int j0, int j1) {
+  int n = 0;
+  for (int j = j0; j < j1 && j < T; ++j) n += T - j;
+  return n;
+}
+
+cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
+                           const ChainDesc* cd, int n_chains, int max_tiles, int* status,
+                           cudaStream_t s) {
+  const int T = max_tiles;
+  for (int K0 = 0; K0 < T; K0 += kPanel) {
+    const int K1 = K0 + kPanel < T ? K0 + kPanel : T;
+    for (int k = K0; k < K1; ++k) {
+      if (k > K0)
+        k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, k, k + 1), n_chains), 128, kTcSmem, s>>>(
+            maps, nullptr, cd, K0, k, k, k + 1, status);
+      k_potrf128<<<n_chains, kPotrfThreads, kPotrfSmem, s>>>(M, Winv, cd, k, status);
+      const int below = T - 1 - k;
+      if (below > 0)
+        k_tc_gemm<TC_TRSM><<<dim3(below, n_chains), 128, kTcSmem, s>>>(maps, wmap, cd, k, k + 1, 0, 0,
+                                                                       status);
+    }
+    if (K1 < T)
+      k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, K1, T), n_chains), 128, kTcSmem, s>>>(
+          maps, nullptr, cd, K0, K1, K1, T, status);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bd

@@ -151,57 +151,105 @@ cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_n
 }
 
 // ---------------------------------------------------------------- form_k
-// One thread per K_kl (k >= l).  D_ab for a != b is read from the strict
-// upper triangle at (min, max) (RPY blocks are symmetric 3 x 3), D_aa = I.
+// K_kl = u_k^T (D_kl - D_k,l+1 - D_k+1,l + D_k+1,l+1) u_l for rods k >= l.
+// CTA per 32 x 32 rod tile (kt >= lt): the 99 x 99 element region of D that
+// the tile needs (beads 32 lt .. 32 lt + 32 against 32 kt .. 32 kt + 32) is
+// staged in shared memory from the strict upper triangle with coalesced row
+// loads; D_ab for a > b is the mirror block (RPY blocks are symmetric), D_aa = I.
+constexpr int KR = 32;        // rods per tile side
+constexpr int KE = 3 * KR + 3;  // 99 elements
+
 template <typename T>
-__device__ __forceinline__ void d_block_times(const T* base, long long np, int a, int b,
-                                              const double* v, double out[3]) {
-  if (a == b) {
-    out[0] = v[0];
-    out[1] = v[1];
-    out[2] = v[2];
-    return;
-  }
-  const int lo = a < b ? a : b, hi = a < b ? b : a;
-  const T* p = base + (long long)(3 * lo) * np + 3 * hi;
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    out[k] = (double)p[k * np] * v[0] + (double)p[k * np + 1] * v[1] + (double)p[k * np + 2] * v[2];
+constexpr int form_k_smem() {
+  return (int)(KE * (KE + 1) * sizeof(T) + 2 * KR * 3 * sizeof(T));
 }
 
+// Arithmetic in the storage type T: K only serves as the Jacobian of the
+// tension iteration (it fixes the convergence rate, not the root), so FP32
+// is enough for the mixed path.
 template <typename T>
 __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __restrict__ K,
                                                 const ChainDesc* __restrict__ cd,
                                                 const double* __restrict__ uhat) {
+  extern __shared__ __align__(16) uint8_t fk_smem[];
+  T (*uk)[3] = reinterpret_cast<T (*)[3]>(fk_smem);
+  T (*ul)[3] = reinterpret_cast<T (*)[3]>(fk_smem + KR * 3 * sizeof(T));
+  T (*R)[KE + 1] = reinterpret_cast<T (*)[KE + 1]>(fk_smem + 2 * KR * 3 * sizeof(T));
   const ChainDesc d = cd[blockIdx.y];
   const int m = d.m;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long npairs = (long long)m * (m + 1) / 2;
-  if (idx >= npairs) return;
-  int k = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
-  while ((long long)k * (k + 1) / 2 > idx) --k;
-  while ((long long)(k + 1) * (k + 2) / 2 <= idx) ++k;
-  const int l = (int)(idx - (long long)k * (k + 1) / 2);  // l <= k
-  const double* uk = uhat + 3 * (d.roff + k);
-  const double* ul = uhat + 3 * (d.roff + l);
+  const int TK = (m + KR - 1) / KR;
+  const int p = blockIdx.x;
+  if (p >= TK * (TK + 1) / 2) return;
+  int kt = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  while (kt * (kt + 1) / 2 > p) --kt;
+  while ((kt + 1) * (kt + 2) / 2 <= p) ++kt;
+  const int lt = p - kt * (kt + 1) / 2;  // lt <= kt
   const T* base = M + d.moff;
   const long long np = d.np;
-  double t0[3], t1[3], t2[3], t3[3];
-  d_block_times(base, np, k, l, ul, t0);
-  d_block_times(base, np, k, l + 1, ul, t1);
-  d_block_times(base, np, k + 1, l, ul, t2);
-  d_block_times(base, np, k + 1, l + 1, ul, t3);
-  double s = 0.0;
+  // R[x][y] = U[3*32*lt + x][3*32*kt + y]: rows from the l side (smaller bead
+  // indices), columns from the k side; only entries with row < col are D.
+  const int row0 = 3 * KR * lt, col0 = 3 * KR * kt;
+  for (int x = threadIdx.x >> 5; x < KE; x += 8) {
+    const int rr = row0 + x;
+    for (int y = threadIdx.x & 31; y < KE; y += 32) {
+      const int cc = col0 + y;
+      T v = T(0);
+      if (rr < d.n && cc < d.n && rr < cc) v = base[(long long)rr * np + cc];
+      R[x][y] = v;
+    }
+  }
+  if (threadIdx.x < KR) {
+    const int t = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) s += uk[q] * (t0[q] - t1[q] - t2[q] + t3[q]);
-  K[d.koff + (long long)k * d.mp + l] = (T)s;
+    for (int q = 0; q < 3; ++q) {
+      uk[t][q] = (KR * kt + t < m) ? (T)uhat[3 * (d.roff + KR * kt + t) + q] : T(0);
+      ul[t][q] = (KR * lt + t < m) ? (T)uhat[3 * (d.roff + KR * lt + t) + q] : T(0);
+    }
+  }
+  __syncthreads();
+  // D_ab v for bead a on the k side (a = 32 kt + ia), b on the l side
+  // (b = 32 lt + ib), ia, ib in [0, 32].
+  auto blk_times = [&](int ia, int ib, const T* v, T out[3]) {
+    const int a = KR * kt + ia, b = KR * lt + ib;
+    if (a == b) {
+      out[0] = v[0];
+      out[1] = v[1];
+      out[2] = v[2];
+      return;
+    }
+    if (b < a) {  // D_ab = D_ba = U[3b..][3a..]
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        out[k] = R[3 * ib + k][3 * ia] * v[0] + R[3 * ib + k][3 * ia + 1] * v[1] +
+                 R[3 * ib + k][3 * ia + 2] * v[2];
+    } else {  // a < b: only on a diagonal tile (kt == lt): U[3a..][3b..]
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        out[k] = R[3 * ia + k][3 * ib] * v[0] + R[3 * ia + k][3 * ib + 1] * v[1] +
+                 R[3 * ia + k][3 * ib + 2] * v[2];
+    }
+  };
+  for (int e = threadIdx.x; e < KR * KR; e += blockDim.x) {
+    const int ia = e / KR, ib = e % KR;  // rod k = 32 kt + ia, rod l = 32 lt + ib
+    const int k = KR * kt + ia, l = KR * lt + ib;
+    if (k >= m || l >= m || l > k) continue;
+    T t0[3], t1[3], t2[3], t3[3];
+    blk_times(ia, ib, ul[ib], t0);
+    blk_times(ia, ib + 1, ul[ib], t1);
+    blk_times(ia + 1, ib, ul[ib], t2);
+    blk_times(ia + 1, ib + 1, ul[ib], t3);
+    T sum = T(0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sum += uk[ia][q] * (t0[q] - t1[q] - t2[q] + t3[q]);
+    K[d.koff + (long long)k * d.mp + l] = sum;
+  }
 }
 
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s) {
-  const long long npairs = (long long)max_m * (max_m + 1) / 2;
-  k_form_k<T><<<dim3(ceil_div(npairs, 256), n_chains), 256, 0, s>>>(M, K, cd, u);
+  const int TK = ceil_div(max_m, KR);
+  k_form_k<T><<<dim3(TK * (TK + 1) / 2, n_chains), 256, form_k_smem<T>(), s>>>(M, K, cd, u);
   return cudaGetLastError();
 }
 
@@ -211,11 +259,153 @@ template cudaError_t launch_trmv<float>(const float*, const ChainDesc*, int, int
                                         const StepArgs*, double, double*, cudaStream_t);
 template cudaError_t launch_symv<double>(const double*, const ChainDesc*, int, int, const double*,
                                          double*, double*, const int*, cudaStream_t);
-template cudaError_t launch_symv<float>(const float*, const ChainDesc*, int, int, const double*,
-                                        double*, double*, const int*, cudaStream_t);
 template cudaError_t launch_form_k<double>(const double*, double*, const ChainDesc*, int, int,
                                            const double*, cudaStream_t);
 template cudaError_t launch_form_k<float>(const float*, float*, const ChainDesc*, int, int,
                                           const double*, cudaStream_t);
+
+}  // namespace bd
+
+namespace bd {
+
+// ---------------------------------------------------- symv, FP32 storage
+// u = D f for D stored in FP32, to FP64-level accuracy without FP64 products:
+// each f value is split into two floats (f = fh + fl), every product d*fh is
+// made exact with an FMA (p + e), the p terms are summed with a compensated
+// (two-sum) accumulator and the small terms in a plain float.  The 128 x 128
+// tile is staged in shared memory; thread t < 128 sums row t, thread t >= 128
+// column t - 128, so each element is read from HBM once and used twice.
+// Diagonal tiles are symmetrised in shared memory (lower part = mirror of the
+// upper, unit diagonal) and only row sums are taken.  Partial sums go to the
+// same two-phase scratch as the FP64 version (tile width 128).
+constexpr int SF = 128;
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_add_prod(DF& a, float d, float fh, float fl) {
+  const float p = d * fh;
+  const float e = fmaf(d, fh, -p);  // exact: d * fh = p + e
+  const float s = a.hi + p;
+  const float bp = s - a.hi;
+  const float err = (a.hi - (s - bp)) + (p - bp);
+  a.hi = s;
+  a.lo += err + e + d * fl;
+}
+
+constexpr int kSymvF32Smem = (SF * (SF + 1) + 4 * SF) * 4;
+
+__global__ void __launch_bounds__(256) k_symv_tiles_f32(const float* __restrict__ M,
+                                                        const ChainDesc* __restrict__ cd,
+                                                        const double* __restrict__ f,
+                                                        double* __restrict__ P,
+                                                        const int* __restrict__ state) {
+  extern __shared__ __align__(16) float sy_smem[];
+  float (*S)[SF + 1] = reinterpret_cast<float (*)[SF + 1]>(sy_smem);
+  float* frh = sy_smem + SF * (SF + 1);
+  float* frl = frh + SF;
+  float* fch = frl + SF;
+  float* fcl = fch + SF;
+  const int c = blockIdx.y;
+  if (state && state[c] >= NS_DONE) return;
+  const ChainDesc d = cd[c];
+  const int TSn = (d.n + SF - 1) / SF;
+  const int p = blockIdx.x;
+  if (p >= TSn * (TSn + 1) / 2) return;
+  int bj = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  while (bj * (bj + 1) / 2 > p) --bj;
+  while ((bj + 1) * (bj + 2) / 2 <= p) ++bj;
+  const int bi = p - bj * (bj + 1) / 2;  // bi <= bj
+  const bool diag = (bi == bj);
+  const int r0 = bi * SF, c0 = bj * SF;
+  const float* base = M + d.moff;
+  const long long np = d.np;
+  // tile load: rows r0.., cols c0.. (within np; zero-padded region is in-bounds)
+  for (int e = threadIdx.x; e < SF * SF / 4; e += 256) {
+    const int r = e / (SF / 4), q = e % (SF / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 + r < d.np && c0 + 4 * q < d.np)
+      v = *reinterpret_cast<const float4*>(base + (long long)(r0 + r) * np + c0 + 4 * q);
+    S[r][4 * q] = v.x;
+    S[r][4 * q + 1] = v.y;
+    S[r][4 * q + 2] = v.z;
+    S[r][4 * q + 3] = v.w;
+  }
+  if (threadIdx.x < SF) {
+    const int q = threadIdx.x;
+    const double* fb = f + 3 * d.boff;
+    const double a = (r0 + q < d.n) ? fb[r0 + q] : 0.0;
+    const double b = (c0 + q < d.n) ? fb[c0 + q] : 0.0;
+    frh[q] = (float)a;
+    frl[q] = (float)(a - (double)frh[q]);
+    fch[q] = (float)b;
+    fcl[q] = (float)(b - (double)fch[q]);
+  }
+  __syncthreads();
+  if (diag) {
+    for (int e = threadIdx.x; e < SF * SF; e += 256) {
+      const int r = e / SF, cc = e % SF;
+      if (cc < r) S[r][cc] = S[cc][r];
+    }
+    __syncthreads();
+    if (threadIdx.x < SF) S[threadIdx.x][threadIdx.x] = 1.0f;
+    __syncthreads();
+  }
+  const long long ld = (long long)TSn * SF;
+  double* Pc = P + d.soff;
+  const int t = threadIdx.x;
+  if (t < SF) {
+    DF acc{0.f, 0.f};
+#pragma unroll 8
+    for (int q = 0; q < SF; ++q) df_add_prod(acc, S[t][q], fch[q], fcl[q]);
+    const double v = (double)acc.hi + (double)acc.lo;
+    Pc[bj * ld + r0 + t] = v;  // rows of bi from column block bj
+  } else if (!diag) {
+    const int q = t - SF;
+    DF acc{0.f, 0.f};
+#pragma unroll 8
+    for (int r = 0; r < SF; ++r) df_add_prod(acc, S[r][q], frh[r], frl[r]);
+    Pc[bi * ld + c0 + q] = (double)acc.hi + (double)acc.lo;  // rows of bj from column block bi
+  }
+}
+
+__global__ void k_symv_reduce_w(const ChainDesc* __restrict__ cd, const double* __restrict__ P,
+                                double* __restrict__ u, const int* __restrict__ state, int width) {
+  const int c = blockIdx.y;
+  if (state && state[c] >= NS_DONE) return;
+  const ChainDesc d = cd[c];
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= d.n) return;
+  const int TSn = (d.n + width - 1) / width;
+  const long long ld = (long long)TSn * width;
+  const double* Pc = P + d.soff;
+  double s = 0.0;
+  for (int t = 0; t < TSn; ++t) s += Pc[t * ld + row];
+  u[3 * d.boff + row] = s;
+}
+
+template <>
+cudaError_t launch_symv<float>(const float* M, const ChainDesc* cd, int n_chains, int max_np,
+                               const double* f, double* scratch, double* u, const int* state,
+                               cudaStream_t s) {
+  const int TSn = ceil_div(max_np, SF);
+  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 256, kSymvF32Smem, s>>>(M, cd, f, scratch,
+                                                                                 state);
+  k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
+  return cudaGetLastError();
+}
+
+cudaError_t matvec_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_symv_tiles_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSymvF32Smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_form_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             form_k_smem<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_form_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             form_k_smem<double>());
+  return e;
+}
 
 }  // namespace bd

@@ -1,0 +1,177 @@
+// k_refine.cu -- Brownian displacement for the mixed-precision path, with
+// one step of iterative refinement against D.
+//
+// The noise term of Sec. 3 Eq. (6) is sqrt(2 dt) B xi with B B^T = D
+// (Eq. (10)).  With a tensor-core factor Lt whose error is E = D - Lt Lt^T,
+// the library uses
+//     y = (s / 2) (Lt xi + D Lt^{-T} xi),  s = sqrt(2 dt),
+// i.e. B_eff = (Lt + D Lt^{-T}) / 2, for which B_eff B_eff^T - D = E D'^{-1} E / 4
+// (D' = Lt Lt^T): the error drops from first to second order in E, with the
+// same xi, so the path stays comparable with the FP64 factor.
+//
+// All three products read FP32 matrices and accumulate in compensated FP32
+// (double-float): each xi or z value is split into two floats, each product
+// d * hi is made exact with an FMA and summed with two-sum, so the results
+// carry FP64-level accuracy without FP64 arithmetic (slow on this part).
+#include "bd_internal.h"
+
+namespace bd {
+
+struct DFa {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void dfa_add_prod(DFa& a, float d, float xh, float xl) {
+  const float p = d * xh;
+  const float e = fmaf(d, xh, -p);
+  const float s = a.hi + p;
+  const float bp = s - a.hi;
+  const float err = (a.hi - (s - bp)) + (p - bp);
+  a.hi = s;
+  a.lo += err + e + d * xl;
+}
+
+__device__ __forceinline__ double dwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Split x (FP64) into two floats per value, x = xh + xl, into the chain's
+// scratch region (xh at [0, n), xl at [n, 2n)), so the product loops below
+// run on FP32 units only.
+__global__ void k_split(const ChainDesc* __restrict__ cd, const double* __restrict__ x_in,
+                        const StepArgs* __restrict__ args, double* __restrict__ scratch) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n) return;
+  const double* x = args ? args->noise + (long long)args->step * args->stride : x_in;
+  const double v = x[3 * d.boff + e];
+  float* xs = reinterpret_cast<float*>(scratch + d.soff);
+  const float h = (float)v;
+  xs[e] = h;
+  xs[d.n + e] = (float)(v - (double)h);
+}
+
+// y1 = Lt x, one warp per row, lanes stride the row.
+__global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
+                                                  const ChainDesc* __restrict__ cd,
+                                                  const double* __restrict__ scratch, double scale,
+                                                  double* __restrict__ y) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* xh = reinterpret_cast<const float*>(scratch + d.soff);
+  const float* xl = xh + d.n;
+  const float* base = M + d.moff;
+  for (int rr = 0; rr < 4; ++rr) {
+    const int row = blockIdx.x * 32 + warp * 4 + rr;
+    if (row >= d.n) return;
+    const float* Lr = base + (long long)row * d.np;
+    DFa acc{0.f, 0.f};
+    for (int c = lane; c <= row; c += 32) dfa_add_prod(acc, Lr[c], xh[c], xl[c]);
+    const double t = dwarp_sum((double)acc.hi + (double)acc.lo);
+    if (lane == 0) y[3 * d.boff + row] = scale * t;
+  }
+}
+
+// z = Lt^{-T} x: one CTA (1024 threads) per chain, 128-row blocks from the
+// last to the first.  Thread t owns columns a = t, t + 1024, ...; after block
+// b is solved (z_b = W_bb^T (x_b - acc_b), W_bb the stored inverse of the
+// diagonal tile) every thread adds sum_{rho in b} Lt[rho][a] z_rho to its
+// columns a < 128 b: each row of Lt is read once, coalesced.
+constexpr int kTrsvThreads = 1024;
+constexpr int kTrsvMaxCols = 12;  // np <= 12288 (N <= 4096)
+
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __restrict__ M,
+                                                             const float* __restrict__ Winv,
+                                                             const ChainDesc* __restrict__ cd,
+                                                             const double* __restrict__ x_in,
+                                                             const StepArgs* __restrict__ args,
+                                                             double* __restrict__ z) {
+  __shared__ double sacc[128], sb[128];
+  __shared__ float zh[128], zl[128], sh[128], sl[128];
+  const ChainDesc d = cd[blockIdx.x];
+  const int T = d.np / kMixedTile;
+  const double* x = args ? args->noise + (long long)args->step * args->stride : x_in;
+  x += 3 * d.boff;
+  const float* base = M + d.moff;
+  const long long np = d.np;
+  const int t = threadIdx.x;
+  DFa acc[kTrsvMaxCols];
+#pragma unroll
+  for (int q = 0; q < kTrsvMaxCols; ++q) acc[q] = DFa{0.f, 0.f};
+  for (int b = T - 1; b >= 0; --b) {
+    const int c0 = 128 * b;
+    // columns of block b owned by this thread: a = t + 1024 q in [c0, c0 + 128)
+#pragma unroll
+    for (int q = 0; q < kTrsvMaxCols; ++q) {
+      const int a = t + kTrsvThreads * q;
+      if (a >= c0 && a < c0 + 128) sacc[a - c0] = (double)acc[q].hi + (double)acc[q].lo;
+    }
+    __syncthreads();
+    if (t < 128) {
+      const int a = c0 + t;
+      const double rhs = ((a < d.n) ? x[a] : 0.0) - sacc[t];
+      sb[t] = rhs;
+      sh[t] = (float)rhs;
+      sl[t] = (float)(rhs - (double)sh[t]);
+    }
+    __syncthreads();
+    if (t < 128) {  // z_i = sum_{j >= i} W[j][i] s_j
+      const float* W = Winv + ((long long)d.wrow + c0) * kMixedTile;
+      DFa zi{0.f, 0.f};
+      for (int j = t; j < 128; ++j) dfa_add_prod(zi, W[j * kMixedTile + t], sh[j], sl[j]);
+      const double v = (double)zi.hi + (double)zi.lo;
+      zh[t] = (float)v;
+      zl[t] = (float)(v - (double)zh[t]);
+      if (c0 + t < d.n) z[3 * d.boff + c0 + t] = v;
+    }
+    __syncthreads();
+    if (b == 0) break;
+    // contributions of block b to every column a < c0
+#pragma unroll
+    for (int q = 0; q < kTrsvMaxCols; ++q) {
+      const int a = t + kTrsvThreads * q;
+      if (a < c0) {
+        const float* col = base + (long long)c0 * np + a;
+        DFa s = acc[q];
+#pragma unroll 4
+        for (int rho = 0; rho < 128; ++rho) dfa_add_prod(s, col[rho * np], zh[rho], zl[rho]);
+        acc[q] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y = scale / 2 (y1 + w)   (scale already applied to y1 when y1 was formed
+// with `scale`; here both y1 and w are unscaled).
+__global__ void k_refine_combine(const ChainDesc* __restrict__ cd, const double* __restrict__ y1,
+                                 const double* __restrict__ w, double half_scale,
+                                 double* __restrict__ y) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n) return;
+  const long long o = 3 * d.boff + e;
+  y[o] = half_scale * (y1[o] + w[o]);
+}
+
+cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
+                                int max_np, const double* x, const StepArgs* args, double scale,
+                                bool refine, double* y, double* y1, double* z, double* w,
+                                double* scratch, cudaStream_t s) {
+  k_split<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, x, args, scratch);
+  if (!refine) {
+    k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
+    return cudaGetLastError();
+  }
+  if (max_np > kTrsvThreads * kTrsvMaxCols) return cudaErrorInvalidValue;
+  k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
+  k_trsv_t_f32<<<n_chains, kTrsvThreads, 0, s>>>(M, Winv, cd, x, args, z);
+  cudaError_t e = launch_symv<float>(M, cd, n_chains, max_np, z, scratch, w, nullptr, s);
+  if (e != cudaSuccess) return e;
+  k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);
+  return cudaGetLastError();
+}
+
+}  // namespace bd

@@ -183,20 +183,35 @@ cudaError_t launch_newton_residual(const double* rstar, const double* u, const C
 }
 
 // ------------------------------------------------------------ Newton solve
-// One CTA per chain: K delta = rhs with K = L_K L_K^T (row-major lower factor
-// of order m, padded to mp), T += delta, iters++, then F(T) for the next
-// mobility product.  Forward sweep right-looking, backward sweep left-looking;
-// 32-row blocks, warps over rows and lanes over columns (coalesced).
+// One CTA (1024 threads) per chain: K delta = rhs with K = L L^T (row-major
+// lower factor of order m, padded to mp) and the stored inverses W_bb of its
+// 32 x 32 diagonal blocks; then T += delta, iters++, and F(T) for the next
+// mobility product.
+//   forward  L z = rhs : block b: s_b = rhs_b - L[b, 0:32b] z (one warp per
+//                        row, lanes along the row), z_b = W_bb s_b;
+//   backward L^T x = z : block b from the last: x_b = W_bb^T (z_b - acc_b),
+//                        then every thread adds L[b rows][a] x_b to the
+//                        columns a < 32b it owns (rows read once, coalesced).
+constexpr int kSolveThreads = 1024;
+constexpr int kSolveCols = 4;   // m <= 4096
+constexpr int kSolveMaxM = kSolveThreads * kSolveCols;
+
+// Accumulation type of the solve: K only preconditions the tension iteration
+// (its accuracy sets the convergence rate, not the root), so the FP32 copy
+// of the mixed path is solved in FP32; the FP64 path stays in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) k_newton_solve(const T* __restrict__ K,
-                                                      const ChainDesc* __restrict__ cd, Phys ph,
-                                                      const double* __restrict__ uhat,
-                                                      double* __restrict__ rhs,
-                                                      double* __restrict__ Tn,
-                                                      double* __restrict__ F,
-                                                      int* __restrict__ state,
-                                                      int* __restrict__ iters) {
-  __shared__ double part[8][32];
+__global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restrict__ K,
+                                                                const T* __restrict__ Kinv,
+                                                                const ChainDesc* __restrict__ cd, Phys ph,
+                                                                const double* __restrict__ uhat,
+                                                                double* __restrict__ rhs,
+                                                                double* __restrict__ Tn,
+                                                                double* __restrict__ F,
+                                                                int* __restrict__ state,
+                                                                int* __restrict__ iters) {
+  extern __shared__ __align__(16) uint8_t ns_smem[];
+  T* zs = reinterpret_cast<T*>(ns_smem);  // [m] solution in the solve's type
+  __shared__ T sblk[32], zblk[32];
   const int c = blockIdx.x;
   const int st = state[c];
   if (st != NS_ACTIVE && st != NS_EXTRA) return;
@@ -204,66 +219,71 @@ __global__ void __launch_bounds__(256) k_newton_solve(const T* __restrict__ K,
   const int m = d.m;
   const long long mp = d.mp;
   const T* L = K + d.koff;
-  double* z = rhs + d.roff;  // solved in place
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* Wb = Kinv + d.kwrow * 32;
+  double* z = rhs + d.roff;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nb = (m + 31) / 32;
-  // forward: L z = rhs
+  for (int e = t; e < m; e += kSolveThreads) zs[e] = (T)z[e];
+  __syncthreads();
+  // forward L y = rhs
   for (int b = 0; b < nb; ++b) {
-    const int r0 = 32 * b;
-    if (warp == 0) {
-      const int row = r0 + lane;
-      double s = (row < m) ? z[row] : 0.0;
-      for (int j = 0; j < 32; ++j) {
-        const int cj = r0 + j;
-        double zj = 0.0;
-        if (lane == j && row < m) zj = s / (double)L[row * mp + row];
-        zj = __shfl_sync(0xffffffffu, zj, j);
-        if (lane > j && row < m && cj < m) s -= (double)L[row * mp + cj] * zj;
-        if (lane == j) s = zj;
-      }
-      if (row < m) z[row] = s;
+    const int r0 = 32 * b, row = r0 + warp;
+    T acc = T(0);
+    if (row < m) {
+      const T* Lr = L + row * mp;
+      for (int q = lane; q < r0; q += 32) acc += Lr[q] * zs[q];
     }
-    __syncthreads();
-    // rows below the block: z[row] -= L[row][r0..r0+31] . z[r0..]
-    const double zb = (r0 + lane < m) ? z[r0 + lane] : 0.0;
-    for (int row = r0 + 32 + warp; row < m; row += 8) {
-      double v = (r0 + lane < m) ? (double)L[row * mp + r0 + lane] * zb : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) z[row] -= v;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sblk[warp] = (row < m) ? zs[row] - acc : T(0);
+    __syncthreads();
+    if (warp == 0) {
+      const T* W = Wb + (long long)r0 * 32;  // W[i][j] at W[i * 32 + j]
+      T v = T(0);
+      for (int j = 0; j <= lane; ++j) v += W[lane * 32 + j] * sblk[j];
+      if (r0 + lane < m) zs[r0 + lane] = v;
     }
     __syncthreads();
   }
-  // backward: L^T x = z
+  // backward L^T x = y
+  T acc[kSolveCols];
+#pragma unroll
+  for (int q = 0; q < kSolveCols; ++q) acc[q] = T(0);
   for (int b = nb - 1; b >= 0; --b) {
     const int c0 = 32 * b;
-    const int col = c0 + lane;
-    double acc = 0.0;
-    for (int row = c0 + 32 + warp; row < m; row += 8)
-      if (col < m) acc += (double)L[row * mp + col] * z[row];
-    part[warp][lane] = acc;
+#pragma unroll
+    for (int q = 0; q < kSolveCols; ++q) {
+      const int a = t + kSolveThreads * q;
+      if (a >= c0 && a < c0 + 32) sblk[a - c0] = ((a < m) ? zs[a] : T(0)) - acc[q];
+    }
     __syncthreads();
     if (warp == 0) {
-      double s = (col < m) ? z[col] : 0.0;
+      const T* W = Wb + (long long)c0 * 32;
+      T v = T(0);  // x_i = sum_{j >= i} W[j][i] s_j
+      for (int j = lane; j < 32; ++j) v += W[j * 32 + lane] * sblk[j];
+      zblk[lane] = v;
+      if (c0 + lane < m) zs[c0 + lane] = v;
+    }
+    __syncthreads();
 #pragma unroll
-      for (int w = 0; w < 8; ++w) s -= part[w][lane];
-      for (int j = 31; j >= 0; --j) {
-        const int cj = c0 + j;
-        double xj = 0.0;
-        if (lane == j && col < m) xj = s / (double)L[col * mp + col];
-        xj = __shfl_sync(0xffffffffu, xj, j);
-        if (lane < j && cj < m && col < m) s -= (double)L[cj * mp + col] * xj;
-        if (lane == j) s = xj;
+    for (int q = 0; q < kSolveCols; ++q) {
+      const int a = t + kSolveThreads * q;
+      if (a < c0) {
+        const T* col = L + (long long)c0 * mp + a;
+        T sacc = T(0);
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r)
+          if (c0 + r < m) sacc += col[r * mp] * zblk[r];
+        acc[q] += sacc;
       }
-      if (col < m) z[col] = s;
     }
     __syncthreads();
   }
   // T += delta
-  for (int k = threadIdx.x; k < m; k += blockDim.x) Tn[d.roff + k] += z[k];
+  for (int k = t; k < m; k += blockDim.x) Tn[d.roff + k] += (double)zs[k];
   __syncthreads();
   // F(T)
-  for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+  for (int i = t; i < d.N; i += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       double f = 0.0;
@@ -272,14 +292,15 @@ __global__ void __launch_bounds__(256) k_newton_solve(const T* __restrict__ K,
       F[3 * (d.boff + i) + q] = f;
     }
   }
-  if (threadIdx.x == 0) iters[c] += 1;
+  if (t == 0) iters[c] += 1;
 }
 
 template <typename T>
-cudaError_t launch_newton_solve(const T* K, const ChainDesc* cd, int n_chains, Phys ph,
+cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F, int* state,
                                 int* iters, cudaStream_t s) {
-  k_newton_solve<T><<<n_chains, 256, 0, s>>>(K, cd, ph, uhat, rhs, Tn, F, state, iters);
+  k_newton_solve<T><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(K, Kinv, cd, ph, uhat, rhs,
+                                                                           Tn, F, state, iters);
   return cudaGetLastError();
 }
 
@@ -402,11 +423,20 @@ cudaError_t launch_set_args(StepArgs* args, const double* noise, long long strid
   return cudaGetLastError();
 }
 
-template cudaError_t launch_newton_solve<double>(const double*, const ChainDesc*, int, Phys,
-                                                 const double*, double*, double*, double*, int*,
-                                                 int*, cudaStream_t);
-template cudaError_t launch_newton_solve<float>(const float*, const ChainDesc*, int, Phys,
-                                                const double*, double*, double*, double*, int*,
+template cudaError_t launch_newton_solve<double>(const double*, const double*, const ChainDesc*, int,
+                                                 Phys, const double*, double*, double*, double*,
+                                                 int*, int*, cudaStream_t);
+template cudaError_t launch_newton_solve<float>(const float*, const float*, const ChainDesc*, int,
+                                                Phys, const double*, double*, double*, double*, int*,
                                                 int*, cudaStream_t);
+
+cudaError_t tension_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kSolveMaxM * sizeof(double)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_newton_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSolveMaxM * sizeof(float)));
+  return e;
+}
 
 }  // namespace bd

@@ -1,0 +1,128 @@
+"""Mixed-precision path (FP32 storage, TF32 tensor-core Cholesky updates,
+FP64 diagonal blocks and tension solve) against the FP64 oracle.
+
+Parity here is not bit-level: the factor carries TF32 rounding (10-bit
+mantissa, unit round-off 2^-11 ~ 4.9e-4).  The bounds below follow from that:
+a backward error ||B B^T - D||_F / ||D||_F of order 1e-4..1e-3 for the raw
+factor, and after the refinement of the Brownian displacement, an error of
+second order in the factor error.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2208_06559_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bd():
+    from paper_2208_06559_gb300 import build as b
+    b.build()
+    import paper_2208_06559_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+MIXED_SIZES = [2, 40, 43, 86, 300, 1000]
+
+
+def test_mixed_factor_backward_error(bd):
+    Nc = np.array(MIXED_SIZES, np.int32)
+    r0 = inputs.random_walk(Nc, 21)
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32)
+    ctx.set_state(cuda(r0))
+    ctx.assemble()
+    ctx.factor()
+    st, _ = ctx.chain_status()
+    assert (st == 0).all(), st
+    off = np.concatenate([[0], np.cumsum(Nc)])
+    for c, N in enumerate(Nc):
+        res = ctx.factor_residual(c)
+        assert res < 2e-3, (N, res)
+        if N <= 300:
+            D = orc.assemble(r0[off[c]:off[c + 1]], 0.25, 0.25)
+            Lref, _ = orc.cholesky(D)
+            L = ctx.read_matrix(c, 1)
+            Dg = ctx.read_matrix(c, 0)
+            np.testing.assert_allclose(Dg, D, rtol=0, atol=1e-6)      # FP32 storage of D
+            assert np.abs(L - Lref).max() < 2e-2 * np.abs(Lref).max(), N
+    ctx.close()
+
+
+def test_mixed_step_constraints_and_displacement(bd):
+    """One step from the same state and noise: rod lengths exact to the
+    Newton tolerance (FP64 solve), displacement close to the FP64 oracle."""
+    Nc = np.array([40, 300, 1000], np.int32)
+    r0 = inputs.random_walk(Nc, 22)
+    noise = inputs.gaussian_noise(1, int(Nc.sum()), 23)
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32, flow=1, Wi=100.0)
+    ctx.set_state(cuda(r0))
+    ctx.step(cuda(noise))
+    r1 = ctx.get_state().cpu().numpy()
+    obs, st = ctx.observables()
+    assert (st == 0).all(), st
+    assert obs[:, 6].max().item() < 1e-10
+    p = orc.make_params(hstar=0.25, dt=1e-4, flow=orc.FLOW_SHEAR, Wi=100.0)
+    rr, *_ = orc.run(p, Nc, r0, noise)
+    disp_err = np.abs((r1 - r0) - (rr - r0)).max() / np.abs(rr - r0).max()
+    assert disp_err < 2e-2, disp_err
+    ctx.close()
+
+
+def test_refined_brownian_displacement(bd):
+    """y = s/2 (Lt xi + D Lt^{-T} xi): matches that formula evaluated in FP64
+    from the library's own Lt and D to FP32 level (the solve with Lt^T uses
+    FP32 inverses of the 128 x 128 diagonal tiles), and the refined factor
+    B_eff = (Lt + D Lt^{-T}) / 2 reproduces D to <= 1e-6 while the raw TF32
+    factor only does to ~1e-4.  B_eff is a different square root of D than
+    the FP64 Cholesky factor L (B_eff - L is first order in the factor
+    error), so the displacement agrees with s L xi only to that order."""
+    Nc = np.array([43, 300], np.int32)
+    r0 = inputs.random_walk(Nc, 31)
+    dt = 1e-4
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32, refine=1, dt=dt)
+    ctx.set_state(cuda(r0))
+    ctx.assemble()
+    ctx.factor()
+    xi = inputs.gaussian_noise(1, int(Nc.sum()), 32)[0]
+    y = ctx.brownian(cuda(xi)).cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(Nc)])
+    s = np.sqrt(2 * dt)
+    for c in range(len(Nc)):
+        sl = slice(off[c], off[c + 1])
+        Lt = ctx.read_matrix(c, 1)
+        D = ctx.read_matrix(c, 0)
+        Beff = 0.5 * (Lt + D @ np.linalg.inv(Lt).T)
+        yref = s * Beff @ xi[sl].ravel()
+        err = np.abs(y[sl].ravel() - yref).max() / np.abs(yref).max()
+        assert err < 1e-6, (c, err)
+        raw = np.linalg.norm(Lt @ Lt.T - D) / np.linalg.norm(D)
+        refined = np.linalg.norm(Beff @ Beff.T - D) / np.linalg.norm(D)
+        assert refined < 1e-6 and refined < raw, (raw, refined)
+        Dx = orc.assemble(r0[sl], 0.25, 0.25)
+        Lx, _ = orc.cholesky(Dx)
+        y64 = s * Lx @ xi[sl].ravel()
+        assert np.abs(y[sl].ravel() - y64).max() / np.abs(y64).max() < 1e-2
+    ctx.close()
+
+
+def test_mixed_without_refinement_is_plain_factor(bd):
+    Nc = np.array([40], np.int32)
+    r0 = inputs.random_walk(Nc, 33)
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32, refine=0)
+    ctx.set_state(cuda(r0))
+    ctx.assemble()
+    ctx.factor()
+    xi = inputs.gaussian_noise(1, 40, 34)[0]
+    y = ctx.brownian(cuda(xi)).cpu().numpy().ravel()
+    Lt = ctx.read_matrix(0, 1)
+    yref = np.sqrt(2e-4) * Lt @ xi.ravel()
+    assert np.abs(y - yref).max() / np.abs(yref).max() < 1e-9
+    ctx.close()
