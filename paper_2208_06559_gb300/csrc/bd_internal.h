@@ -9,7 +9,7 @@
 //     is not stored.  Rows and columns past 3 N_c are an identity border, so
 //     the padded matrix factors to diag(L, I);
 //   * per chain a second square matrix of order mp_c (N_c - 1 rounded up to
-//     32) for the rod-coupling matrix K = U^T C^T D C U and its factor;
+//     64) for the rod-coupling matrix K = U^T C^T D C U and its factor;
 //   * FP64 (BD_FP64) or FP32 (mixed) element type for both matrices.
 #pragma once
 #include <cuda.h>
@@ -85,9 +85,11 @@ template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s);
 
+cudaError_t launch_rod_dirs(const double* r, const ChainDesc* cd, int n_chains, int max_N,
+                            double* uhat, cudaStream_t s);
 cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd,
                              int n_chains, int max_N, Phys ph, double* rstar,
-                             double* uhat, double* T, double* F, int* state,
+                             const double* uhat, double* T, double* F, int* state,
                              const int* status, int* iters, cudaStream_t s);
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs,
@@ -107,16 +109,24 @@ cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chain
                                const int* iters, double* obs, cudaStream_t s);
 cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
                             cudaStream_t s);
+// FP32 Cholesky of the rod-coupling matrix with 64-wide tiles (k_chol_k64.cu);
+// mp must be a multiple of 64; the 64 x 64 diagonal-tile inverses go to Kinv.
+cudaError_t k64_configure();
+cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
+                            int* status, cudaStream_t s);
+
 // Opt-in shared-memory sizes of the matvec kernels (once per device).
 cudaError_t matvec_configure();
 cudaError_t tension_configure();
 
 // Mixed-precision Brownian displacement with one refinement step (k_refine.cu):
 // y = s/2 (B xi + D B^{-T} xi); with refine == 0, y = s B xi.
+// The triangular solve of the refinement runs on `s2` (forked from and joined
+// back into `s` with events ev[0], ev[1]) concurrently with the product.
 cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
-                                double* scratch, cudaStream_t s);
+                                double* scratch, cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev);
 
 // Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
 bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains);

@@ -62,6 +62,9 @@ struct bd_ctx {
   std::vector<int> group_tiles;      // max 128-tiles of each group
   cudaStream_t gs[kMaxGroups] = {};
   cudaEvent_t gev[kMaxGroups + 1] = {};
+  // concurrent branches of the step: the K chain, the refinement's solve
+  cudaStream_t aux[2] = {};
+  cudaEvent_t aev[4] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool have_state = false;
@@ -134,7 +137,8 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
   const double sc = c->ph.sq2dt;
   if (c->mixed)  // buffers rT, F, u are free at this point of the step
     CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, x, args, sc,
-                           c->p.refine != 0, y, c->rT, c->F, c->u, c->scratch, s));
+                           c->p.refine != 0, y, c->rT, c->F, c->u, c->scratch, s, c->aux[1],
+                           c->aev + 2));
   else
     CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
   return BD_OK;
@@ -150,24 +154,33 @@ int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaSt
   return BD_OK;
 }
 
+// Before the tension solve.  The K chain (rod directions, K, its factor)
+// needs only the old positions and the upper-triangle D, so it runs on its
+// own stream while D is factored and the Brownian displacement is formed.
 int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   int rc;
   if ((rc = enqueue_assemble(c, s))) return rc;
-  if ((rc = enqueue_factor(c, s))) return rc;
-  if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
-  CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
-                      c->F, c->state, c->status, c->iters, s));
+  cudaStream_t sk = c->aux[0];
+  CK(cudaEventRecord(c->aev[0], s));
+  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  CK(launch_rod_dirs(c->r, c->d_cd, c->n_chains, c->max_N, c->uhat, sk));
   if (c->mixed) {
     CK(launch_form_k<float>((const float*)c->M, (float*)c->K, c->d_cd, c->n_chains, c->max_m,
-                            c->uhat, s));
-    CK(launch_chol_simt<float>((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains,
-                               c->max_mp / kSimtTile, true, c->status, s));
+                            c->uhat, sk));
+    CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64,
+                       c->status, sk));
   } else {
     CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
-                             c->uhat, s));
+                             c->uhat, sk));
     CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
-                                c->max_mp / kSimtTile, true, c->status, s));
+                                c->max_mp / kSimtTile, true, c->status, sk));
   }
+  CK(cudaEventRecord(c->aev[1], sk));
+  if ((rc = enqueue_factor(c, s))) return rc;
+  if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
+  CK(cudaStreamWaitEvent(s, c->aev[1], 0));
+  CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
+                      c->F, c->state, c->status, c->iters, s));
   return BD_OK;
 }
 
@@ -381,6 +394,10 @@ void bd_destroy(bd_ctx* c) {
     if (c->gs[g]) cudaStreamDestroy(c->gs[g]);
   for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
     if (c->gev[g]) cudaEventDestroy(c->gev[g]);
+  for (int g = 0; g < 2; ++g)
+    if (c->aux[g]) cudaStreamDestroy(c->aux[g]);
+  for (int g = 0; g < 4; ++g)
+    if (c->aev[g]) cudaEventDestroy(c->aev[g]);
   if (c->cs) cudaStreamDestroy(c->cs);
   if (c->cs2) cudaStreamDestroy(c->cs2);
   delete c;
@@ -444,7 +461,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     d.n = 3 * d.N;
     d.np = (int)round_up(d.n, c->tileM);
     d.m = d.N - 1;
-    d.mp = (int)round_up(d.m, kSimtTile);
+    d.mp = (int)round_up(d.m, 2 * kSimtTile);
     d.boff = boff;
     d.roff = roff;
     d.moff = moff;
@@ -497,7 +514,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
             alloc((void**)&c->iters, sizeof(int) * c->n_chains) &&
             alloc((void**)&c->args, sizeof(StepArgs)) &&
             alloc((void**)&c->loops, sizeof(unsigned long long));
-  ok = ok && alloc(&c->Kinv, (size_t)kwrow * kSimtTile * c->elem) &&
+  ok = ok && alloc(&c->Kinv, (size_t)kwrow * 64 * c->elem) &&
        (c->mixed || alloc(&c->Minv, (size_t)swrow * kSimtTile * c->elem));
   if (ok && c->mixed)
     ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
@@ -511,8 +528,13 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     return code;
   };
   if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking) != cudaSuccess)
     return fail(BD_ERR_CUDA);
+  for (int g = 0; g < 4; ++g)
+    if (cudaEventCreateWithFlags(&c->aev[g], cudaEventDisableTiming) != cudaSuccess)
+      return fail(BD_ERR_CUDA);
   cudaStream_t s = c->cs;
   if (c->mixed) {
     c->n_groups = c->n_chains / 16;
@@ -541,7 +563,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
         tc_configure() != cudaSuccess)
       return fail(BD_ERR_CUDA);
   }
-  if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess)
+  if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
+      k64_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -272,13 +272,15 @@ namespace bd {
 // u = D f for D stored in FP32, to FP64-level accuracy without FP64 products:
 // each f value is split into two floats (f = fh + fl), every product d*fh is
 // made exact with an FMA (p + e), the p terms are summed with a compensated
-// (two-sum) accumulator and the small terms in a plain float.  The 128 x 128
-// tile is staged in shared memory; thread t < 128 sums row t, thread t >= 128
-// column t - 128, so each element is read from HBM once and used twice.
-// Diagonal tiles are symmetrised in shared memory (lower part = mirror of the
-// upper, unit diagonal) and only row sums are taken.  Partial sums go to the
-// same two-phase scratch as the FP64 version (tile width 128).
-constexpr int SF = 128;
+// (two-sum) accumulator and the small terms in a plain float.  A 64 x 64 tile
+// is staged in shared memory (128 threads: thread t < 64 sums row t, thread
+// t >= 64 column t - 64), so each element is read from HBM once and used
+// twice; small CTAs let about a dozen share an SM, overlapping one tile's
+// loads with another's sums.  Diagonal tiles are symmetrised in shared memory
+// (mirror of the upper part, unit diagonal) and only row sums are taken.
+// Partial sums go to the same two-phase scratch as the FP64 version.
+constexpr int SF = 64;
+constexpr int SFP = SF + 4;  // row pitch: 16-byte aligned rows for float4 access
 
 struct DF {
   float hi, lo;
@@ -294,19 +296,15 @@ __device__ __forceinline__ void df_add_prod(DF& a, float d, float fh, float fl) 
   a.lo += err + e + d * fl;
 }
 
-constexpr int kSymvF32Smem = (SF * (SF + 1) + 4 * SF) * 4;
+constexpr int kSymvF32Smem = (SF * SFP + 4 * SF) * 4;
 
-__global__ void __launch_bounds__(256) k_symv_tiles_f32(const float* __restrict__ M,
+__global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict__ M,
                                                         const ChainDesc* __restrict__ cd,
                                                         const double* __restrict__ f,
                                                         double* __restrict__ P,
                                                         const int* __restrict__ state) {
-  extern __shared__ __align__(16) float sy_smem[];
-  float (*S)[SF + 1] = reinterpret_cast<float (*)[SF + 1]>(sy_smem);
-  float* frh = sy_smem + SF * (SF + 1);
-  float* frl = frh + SF;
-  float* fch = frl + SF;
-  float* fcl = fch + SF;
+  __shared__ __align__(16) float S[SF][SFP];
+  __shared__ float frh[SF], frl[SF], fch[SF], fcl[SF];
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
@@ -319,48 +317,49 @@ __global__ void __launch_bounds__(256) k_symv_tiles_f32(const float* __restrict_
   const int bi = p - bj * (bj + 1) / 2;  // bi <= bj
   const bool diag = (bi == bj);
   const int r0 = bi * SF, c0 = bj * SF;
-  const float* base = M + d.moff;
+  const float* base = M + d.moff + (long long)r0 * d.np + c0;
   const long long np = d.np;
-  // tile load: rows r0.., cols c0.. (within np; zero-padded region is in-bounds)
-  for (int e = threadIdx.x; e < SF * SF / 4; e += 256) {
-    const int r = e / (SF / 4), q = e % (SF / 4);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r0 + r < d.np && c0 + 4 * q < d.np)
-      v = *reinterpret_cast<const float4*>(base + (long long)(r0 + r) * np + c0 + 4 * q);
-    S[r][4 * q] = v.x;
-    S[r][4 * q + 1] = v.y;
-    S[r][4 * q + 2] = v.z;
-    S[r][4 * q + 3] = v.w;
+  const int t = threadIdx.x;
+  // rows r0 .. r0 + 63 and columns c0 .. c0 + 63 lie inside the padded matrix
+#pragma unroll
+  for (int q = 0; q < SF * SF / 4 / 128; ++q) {
+    const int e = t + 128 * q;
+    const int r = e >> 4, c4 = e & 15;
+    *reinterpret_cast<float4*>(&S[r][4 * c4]) =
+        __ldg(reinterpret_cast<const float4*>(base + (long long)r * np + 4 * c4));
   }
-  if (threadIdx.x < SF) {
-    const int q = threadIdx.x;
+  if (t < SF) {
     const double* fb = f + 3 * d.boff;
-    const double a = (r0 + q < d.n) ? fb[r0 + q] : 0.0;
-    const double b = (c0 + q < d.n) ? fb[c0 + q] : 0.0;
-    frh[q] = (float)a;
-    frl[q] = (float)(a - (double)frh[q]);
-    fch[q] = (float)b;
-    fcl[q] = (float)(b - (double)fch[q]);
+    const double a = (r0 + t < d.n) ? fb[r0 + t] : 0.0;
+    const double b = (c0 + t < d.n) ? fb[c0 + t] : 0.0;
+    frh[t] = (float)a;
+    frl[t] = (float)(a - (double)frh[t]);
+    fch[t] = (float)b;
+    fcl[t] = (float)(b - (double)fch[t]);
   }
   __syncthreads();
   if (diag) {
-    for (int e = threadIdx.x; e < SF * SF; e += 256) {
-      const int r = e / SF, cc = e % SF;
+    for (int e = t; e < SF * SF; e += 128) {
+      const int r = e >> 6, cc = e & 63;
       if (cc < r) S[r][cc] = S[cc][r];
     }
     __syncthreads();
-    if (threadIdx.x < SF) S[threadIdx.x][threadIdx.x] = 1.0f;
+    if (t < SF) S[t][t] = 1.0f;
     __syncthreads();
   }
   const long long ld = (long long)TSn * SF;
   double* Pc = P + d.soff;
-  const int t = threadIdx.x;
   if (t < SF) {
     DF acc{0.f, 0.f};
-#pragma unroll 8
-    for (int q = 0; q < SF; ++q) df_add_prod(acc, S[t][q], fch[q], fcl[q]);
-    const double v = (double)acc.hi + (double)acc.lo;
-    Pc[bj * ld + r0 + t] = v;  // rows of bi from column block bj
+#pragma unroll 4
+    for (int q4 = 0; q4 < SF / 4; ++q4) {
+      const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
+      df_add_prod(acc, v.x, fch[4 * q4], fcl[4 * q4]);
+      df_add_prod(acc, v.y, fch[4 * q4 + 1], fcl[4 * q4 + 1]);
+      df_add_prod(acc, v.z, fch[4 * q4 + 2], fcl[4 * q4 + 2]);
+      df_add_prod(acc, v.w, fch[4 * q4 + 3], fcl[4 * q4 + 3]);
+    }
+    Pc[bj * ld + r0 + t] = (double)acc.hi + (double)acc.lo;  // rows of bi from column block bj
   } else if (!diag) {
     const int q = t - SF;
     DF acc{0.f, 0.f};
@@ -390,17 +389,13 @@ cudaError_t launch_symv<float>(const float* M, const ChainDesc* cd, int n_chains
                                const double* f, double* scratch, double* u, const int* state,
                                cudaStream_t s) {
   const int TSn = ceil_div(max_np, SF);
-  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 256, kSymvF32Smem, s>>>(M, cd, f, scratch,
-                                                                                 state);
+  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state);
   k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
   return cudaGetLastError();
 }
 
 cudaError_t matvec_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_symv_tiles_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSymvF32Smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_form_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_form_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              form_k_smem<float>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_form_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,

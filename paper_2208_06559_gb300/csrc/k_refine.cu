@@ -159,16 +159,22 @@ __global__ void k_refine_combine(const ChainDesc* __restrict__ cd, const double*
 cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
-                                double* scratch, cudaStream_t s) {
+                                double* scratch, cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev) {
   k_split<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, x, args, scratch);
   if (!refine) {
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
     return cudaGetLastError();
   }
   if (max_np > kTrsvThreads * kTrsvMaxCols) return cudaErrorInvalidValue;
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
+  if (e != cudaSuccess) return e;
+  k_trsv_t_f32<<<n_chains, kTrsvThreads, 0, s2>>>(M, Winv, cd, x, args, z);
   k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
-  k_trsv_t_f32<<<n_chains, kTrsvThreads, 0, s>>>(M, Winv, cd, x, args, z);
-  cudaError_t e = launch_symv<float>(M, cd, n_chains, max_np, z, scratch, w, nullptr, s);
+  e = cudaEventRecord(ev[1], s2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+  if (e != cudaSuccess) return e;
+  e = launch_symv<float>(M, cd, n_chains, max_np, z, scratch, w, nullptr, s);
   if (e != cudaSuccess) return e;
   k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);
   return cudaGetLastError();

@@ -58,12 +58,35 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
+// ------------------------------------------------------------ rod directions
+// u_k = Q_k / |Q_k| at the positions of the start of the step: the directions
+// along which the rod tensions act (and the right factor of K).
+__global__ void k_rod_dirs(const double* __restrict__ r, const ChainDesc* __restrict__ cd,
+                           double* __restrict__ uhat) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.m) return;
+  const double* a0 = r + 3 * (d.boff + k);
+  const double q0 = a0[3] - a0[0], q1 = a0[4] - a0[1], q2 = a0[5] - a0[2];
+  const double inv = 1.0 / sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+  double* u = uhat + 3 * (d.roff + k);
+  u[0] = q0 * inv;
+  u[1] = q1 * inv;
+  u[2] = q2 * inv;
+}
+
+cudaError_t launch_rod_dirs(const double* r, const ChainDesc* cd, int n_chains, int max_N,
+                            double* uhat, cudaStream_t s) {
+  k_rod_dirs<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, cd, uhat);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ predictor
 // r* = r + dt kappa.r + y; u_k = Q_k / |Q_k| at the old positions;
 // T0_k = (|Q*_k| - 1) / (2 dt); F0 = F(T0).  One thread per bead.
 __global__ void k_predictor(const double* __restrict__ r, const double* __restrict__ y,
                             const ChainDesc* __restrict__ cd, int n_chains, Phys ph,
-                            double* __restrict__ rstar, double* __restrict__ uhat,
+                            double* __restrict__ rstar, const double* __restrict__ uhat,
                             double* __restrict__ T, double* __restrict__ F,
                             int* __restrict__ state, const int* __restrict__ status,
                             int* __restrict__ iters) {
@@ -84,45 +107,39 @@ __global__ void k_predictor(const double* __restrict__ r, const double* __restri
       out[k] = rb[k] + ph.dt * kr + yb[k];
     }
   };
+  // T0 of rod j from |Q*_j| (self-only, K* -> infinity limit of Eq. (17))
+  auto t0 = [&](const double* ra, const double* rb) {
+    const double q0 = rb[0] - ra[0], q1 = rb[1] - ra[1], q2 = rb[2] - ra[2];
+    return (sqrt(q0 * q0 + q1 * q1 + q2 * q2) - 1.0) / (2.0 * ph.dt);
+  };
   double ri[3];
   pred(i, ri);
 #pragma unroll
   for (int k = 0; k < 3; ++k) rstar[3 * (d.boff + i) + k] = ri[k];
-  double ui[3] = {0, 0, 0}, Ti = 0.0;
+  double Fi[3] = {0.0, 0.0, 0.0};
   if (i < d.m) {
     double rn[3];
     pred(i + 1, rn);
-    const double* a0 = r + 3 * (d.boff + i);
-    double q[3] = {a0[3] - a0[0], a0[4] - a0[1], a0[5] - a0[2]};
-    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
-    const double qs0 = rn[0] - ri[0], qs1 = rn[1] - ri[1], qs2 = rn[2] - ri[2];
-    Ti = (sqrt(qs0 * qs0 + qs1 * qs1 + qs2 * qs2) - 1.0) / (2.0 * ph.dt);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      ui[k] = q[k] / qn;
-      uhat[3 * (d.roff + i) + k] = ui[k];
-    }
+    const double Ti = t0(ri, rn);
     T[d.roff + i] = Ti;
+    const double* ui = uhat + 3 * (d.roff + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fi[k] += Ti * ui[k];
   }
-  // F_i = T_i u_i - T_{i-1} u_{i-1}: the previous rod's values are recomputed
-  double Fi[3] = {Ti * ui[0], Ti * ui[1], Ti * ui[2]};
-  if (i > 0) {
+  if (i > 0) {  // F_i = T_i u_i - T_{i-1} u_{i-1}; the previous rod's T0 is recomputed
     double rp[3];
     pred(i - 1, rp);
-    const double* a0 = r + 3 * (d.boff + i - 1);
-    double q[3] = {a0[3] - a0[0], a0[4] - a0[1], a0[5] - a0[2]};
-    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
-    const double qs0 = ri[0] - rp[0], qs1 = ri[1] - rp[1], qs2 = ri[2] - rp[2];
-    const double Tp = (sqrt(qs0 * qs0 + qs1 * qs1 + qs2 * qs2) - 1.0) / (2.0 * ph.dt);
+    const double Tp = t0(rp, ri);
+    const double* up = uhat + 3 * (d.roff + i - 1);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) Fi[k] -= Tp * (q[k] / qn);
+    for (int k = 0; k < 3; ++k) Fi[k] -= Tp * up[k];
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[3 * (d.boff + i) + k] = Fi[k];
 }
 
 cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd, int n_chains,
-                             int max_N, Phys ph, double* rstar, double* uhat, double* T, double* F,
+                             int max_N, Phys ph, double* rstar, const double* uhat, double* T, double* F,
                              int* state, const int* status, int* iters, cudaStream_t s) {
   k_predictor<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, y, cd, n_chains, ph, rstar,
                                                                     uhat, T, F, state, status, iters);
@@ -199,7 +216,7 @@ constexpr int kSolveMaxM = kSolveThreads * kSolveCols;
 // Accumulation type of the solve: K only preconditions the tension iteration
 // (its accuracy sets the convergence rate, not the root), so the FP32 copy
 // of the mixed path is solved in FP32; the FP64 path stays in FP64.
-template <typename T>
+template <typename T, int BS>
 __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restrict__ K,
                                                                 const T* __restrict__ Kinv,
                                                                 const ChainDesc* __restrict__ cd, Phys ph,
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
                                                                 int* __restrict__ iters) {
   extern __shared__ __align__(16) uint8_t ns_smem[];
   T* zs = reinterpret_cast<T*>(ns_smem);  // [m] solution in the solve's type
-  __shared__ T sblk[32], zblk[32];
+  __shared__ T sblk[BS], zblk[BS];
   const int c = blockIdx.x;
   const int st = state[c];
   if (st != NS_ACTIVE && st != NS_EXTRA) return;
@@ -219,29 +236,34 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
   const int m = d.m;
   const long long mp = d.mp;
   const T* L = K + d.koff;
-  const T* Wb = Kinv + d.kwrow * 32;
+  const T* Wb = Kinv + d.kwrow * BS;
   double* z = rhs + d.roff;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int nb = (m + 31) / 32;
+  constexpr int RPW = BS / 32;  // rows per warp in a block
+  const int nb = (m + BS - 1) / BS;
   for (int e = t; e < m; e += kSolveThreads) zs[e] = (T)z[e];
   __syncthreads();
   // forward L y = rhs
   for (int b = 0; b < nb; ++b) {
-    const int r0 = 32 * b, row = r0 + warp;
-    T acc = T(0);
-    if (row < m) {
-      const T* Lr = L + row * mp;
-      for (int q = lane; q < r0; q += 32) acc += Lr[q] * zs[q];
-    }
+    const int r0 = BS * b;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sblk[warp] = (row < m) ? zs[row] - acc : T(0);
+    for (int q = 0; q < RPW; ++q) {
+      const int lr = warp * RPW + q, row = r0 + lr;
+      T acc = T(0);
+      if (row < m) {
+        const T* Lr = L + row * mp;
+        for (int cc = lane; cc < r0; cc += 32) acc += Lr[cc] * zs[cc];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) sblk[lr] = (row < m) ? zs[row] - acc : T(0);
+    }
     __syncthreads();
-    if (warp == 0) {
-      const T* W = Wb + (long long)r0 * 32;  // W[i][j] at W[i * 32 + j]
+    if (t < BS) {
+      const T* W = Wb + (long long)r0 * BS;  // W[i][j] at W[i * BS + j]
       T v = T(0);
-      for (int j = 0; j <= lane; ++j) v += W[lane * 32 + j] * sblk[j];
-      if (r0 + lane < m) zs[r0 + lane] = v;
+      for (int j = 0; j <= t; ++j) v += W[t * BS + j] * sblk[j];
+      if (r0 + t < m) zs[r0 + t] = v;
     }
     __syncthreads();
   }
@@ -250,19 +272,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
 #pragma unroll
   for (int q = 0; q < kSolveCols; ++q) acc[q] = T(0);
   for (int b = nb - 1; b >= 0; --b) {
-    const int c0 = 32 * b;
+    const int c0 = BS * b;
 #pragma unroll
     for (int q = 0; q < kSolveCols; ++q) {
       const int a = t + kSolveThreads * q;
-      if (a >= c0 && a < c0 + 32) sblk[a - c0] = ((a < m) ? zs[a] : T(0)) - acc[q];
+      if (a >= c0 && a < c0 + BS) sblk[a - c0] = ((a < m) ? zs[a] : T(0)) - acc[q];
     }
     __syncthreads();
-    if (warp == 0) {
-      const T* W = Wb + (long long)c0 * 32;
+    if (t < BS) {
+      const T* W = Wb + (long long)c0 * BS;
       T v = T(0);  // x_i = sum_{j >= i} W[j][i] s_j
-      for (int j = lane; j < 32; ++j) v += W[j * 32 + lane] * sblk[j];
-      zblk[lane] = v;
-      if (c0 + lane < m) zs[c0 + lane] = v;
+      for (int j = t; j < BS; ++j) v += W[j * BS + t] * sblk[j];
+      zblk[t] = v;
+      if (c0 + t < m) zs[c0 + t] = v;
     }
     __syncthreads();
 #pragma unroll
@@ -272,7 +294,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
         const T* col = L + (long long)c0 * mp + a;
         T sacc = T(0);
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r)
+        for (int r = 0; r < BS; ++r)
           if (c0 + r < m) sacc += col[r * mp] * zblk[r];
         acc[q] += sacc;
       }
@@ -295,12 +317,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
   if (t == 0) iters[c] += 1;
 }
 
+// the FP64 path factors K with 32-wide tiles, the mixed path with 64-wide ones
+template <typename T>
+constexpr int solve_block() {
+  return sizeof(T) == 8 ? 32 : 64;
+}
+
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F, int* state,
                                 int* iters, cudaStream_t s) {
-  k_newton_solve<T><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(K, Kinv, cd, ph, uhat, rhs,
-                                                                           Tn, F, state, iters);
+  k_newton_solve<T, solve_block<T>()><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(
+      K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters);
   return cudaGetLastError();
 }
 
@@ -431,10 +459,11 @@ template cudaError_t launch_newton_solve<float>(const float*, const float*, cons
                                                 int*, cudaStream_t);
 
 cudaError_t tension_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double, 32>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(kSolveMaxM * sizeof(double)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_newton_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_newton_solve<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSolveMaxM * sizeof(float)));
   return e;
 }
