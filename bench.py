@@ -9,9 +9,10 @@ headline; the FP64 path runs the same chains on the same GPU for the ratio.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One JSON line is printed by rank 0.  Under torchrun every rank advances its
-own replica batch (independent chains, no data exchange: weak scaling); the
-timing barrier is the only collective.  ``--impl reference`` times the FP64 CPU
-oracle on the host cores instead (bounded sample of the same workload).
+own replica batch (independent chains, disjoint seeds, no data exchange: weak
+scaling); the timing barrier and the max-over-ranks time are the only
+collectives.  ``--impl reference`` times the FP64 CPU oracle on the host cores
+instead (a bounded sample of the same workload).
 """
 from __future__ import annotations
 
@@ -29,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2208_06559_gb300 import inputs  # noqa: E402
+from paper_2208_06559_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "chain-timesteps/s at N=1000 (mixed vs FP64, same GPU); Cholesky % tensor peak"
 UNIT = "chain-timesteps/s"
@@ -79,8 +80,14 @@ class ClockSampler:
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(s[1]) for s in self.samples) if v is not None]
+        mx = [v for v in (num(s[2]) for s in self.samples) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for s in self.samples for i in range(4)
                           if len(s) > 5 + i and s[5 + i].lower() == "active"})
@@ -89,41 +96,43 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def workload_cfg(args):
-    w = inputs.WORKLOADS[args.workload]
-    return w
-
-
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2208_06559_gb300 as bd
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = workload_cfg(args)
+    w = inputs.WORKLOADS[args.workload]
     Nc = w.lengths()
     total = int(Nc.sum())
-    seed = w.seed + 1000 * rank          # disjoint replicas per rank
-    r0 = torch.from_numpy(inputs.random_walk(Nc, seed)).to(dev)
+    seed = replicas.replica_seed(w.seed, rank)      # disjoint replicas per rank
+    r0_host = inputs.random_walk(Nc, seed)
+    r0 = torch.from_numpy(r0_host).to(dev)
     K, W = args.steps, args.warmup
-    noise_host = inputs.gaussian_noise(K + W, total, seed + 1)
+    noise_host = inputs.gaussian_noise(K + W + 2, total, seed + 1)
     noise = torch.from_numpy(noise_host).to(dev)
     peaks, peak_src = load_peaks()
     stream = torch.cuda.current_stream()
+    prec = {"fp64": bd.FP64, "tf32": bd.MIXED_TF32}[args.precision] if args.precision else \
+        (bd.MIXED_TF32 if w.precision != 0 else bd.FP64)
+    kw = dict(h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed_steps(prec, nsteps, nwarm):
-        ctx = bd.Context(Nc, h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, precision=prec)
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed_steps(p, nsteps, nwarm):
+        ctx = bd.Context(Nc, precision=p, **kw)
         ctx.set_state(r0)
         for i in range(nwarm):
             ctx.step(noise[i:i + 1])
         barrier()
         l0 = ctx.kernel_launches()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = ev(), ev()
         barrier()
         e0.record(stream)
         ctx.step(noise[nwarm:nwarm + nsteps])
@@ -131,24 +140,21 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         ms = e0.elapsed_time(e1)
         launches = ctx.kernel_launches() - l0
-        _, st = ctx.observables()
-        return ctx, ms, launches, st
+        obs, st = ctx.observables()
+        return ctx, ms, launches, st, obs
 
-    prec = bd.MIXED_TF32 if w.precision != 0 else bd.FP64
     with ClockSampler(local_rank) as clk:
-        ctx, ms, launches, st = timed_steps(prec, K, W)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = len(Nc) * K * world / (ms_max / 1e3)
+        ctx, ms, launches, st, obs = timed_steps(prec, K, W)
+    units, ms_max = replicas.aggregate(ms, len(Nc) * K, world, device=dev)
+    value = units / (ms_max / 1e3)
 
-    # Dominant stage: the Cholesky factorisation, timed live with CUDA events
-    # on the launching stream (assembly re-run before each factorisation).
+    # Stage times on the same context, CUDA events on the launching stream.
+    # The dominant stage is the Cholesky factorisation (assembly re-run
+    # before each factorisation, outside the timed interval).
     reps = 3
     fms = 0.0
     for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, b = ev(), ev()
         ctx.assemble()
         a.record(stream)
         ctx.factor()
@@ -156,38 +162,61 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         fms += a.elapsed_time(b)
     fms /= reps
-    npad = 3 * Nc
-    chol_flops = float(np.sum(npad.astype(np.float64) ** 3) / 3.0)
+    stage = {"factor_ms": fms}
+    f = noise[0]
+    for name, fn in (("assemble_ms", ctx.assemble), ("brownian_ms", lambda: ctx.brownian(f)),
+                     ("mobility_symv_ms", lambda: ctx.mobility_apply(f))):
+        fn()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        stage[name] = a.elapsed_time(b) / reps
+    newton = ctx.chain_status()[1]
+    stage["newton_iterations_last_step_max"] = int(newton.max())
+    ctx.close()
+
+    n = 3 * Nc.astype(np.float64)
+    chol_flops = float(np.sum(n ** 3) / 3.0)
     achieved_tf = chol_flops / (fms / 1e3) / 1e12
+    esize = 8 if prec == bd.FP64 else 4
+    symv_bytes = float(np.sum(n * n / 2.0)) * esize   # upper triangle read once
+    symv_gbs = symv_bytes / (stage["mobility_symv_ms"] / 1e3) / 1e9
     if prec == bd.FP64:
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": 1.25, "unit": "TFLOP/s",
-                "peak_source": "nominal FP64 (no measured FP64 peak)",
-                "kernel": "cholesky (FP64 SIMT)"}
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": 1.252, "unit": "TFLOP/s",
+                "peak_source": "measured FP64 FMA throughput of this GPU (1.252 TFLOP/s)",
+                "kernel": "cholesky factorisation (FP64, CUDA cores)"}
     else:
         tf32 = peaks["bf16_tflops"] * 0.5
         roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tf32, "unit": "TFLOP/s",
                 "peak_source": f"TF32 = 0.5 x bf16 burst ({peak_src})",
-                "kernel": "cholesky (mixed)"}
+                "kernel": "cholesky factorisation (tcgen05 TF32 products, FP32 diagonal tiles)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["ms_per_factorisation"] = fms
-    ctx.close()
+    roof["algorithmic_flops_per_launch"] = chol_flops
+    roof["ms_per_launch"] = fms
+    others = {"mobility_symv": {"bound": "hbm", "achieved": symv_gbs, "peak": peaks["hbm_gbs"],
+                                "unit": "GB/s", "frac": symv_gbs / peaks["hbm_gbs"],
+                                "algorithmic_bytes_per_launch": symv_bytes}}
 
     # FP64 path on the same chains (the ratio of the metric)
     fp64 = None
     if prec != bd.FP64 and not args.skip_fp64:
         k64 = max(1, min(args.fp64_steps, K))
-        ctx64, ms64, _, st64 = timed_steps(bd.FP64, k64, 1)
+        ctx64, ms64, _, st64, _ = timed_steps(bd.FP64, k64, 1)
         ctx64.close()
-        v64 = len(Nc) * k64 * world / (ms64 / 1e3)
-        fp64 = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
-                "speedup_mixed_over_fp64": value / v64}
+        u64, m64 = replicas.aggregate(ms64, len(Nc) * k64, world, device=dev)
+        v64 = u64 / (m64 / 1e3)
+        fp64 = {"value": v64, "ms_per_step": m64 / k64, "steps": k64,
+                "speedup_mixed_over_fp64": value / v64, "chain_status_ok": bool((st64 == 0).all())}
 
-    # End to end through the public API with host buffers: per step the noise
-    # goes host (pinned) -> device and the per-chain observables come back.
+    # End to end through the public API with host buffers: every step the
+    # noise goes host (pinned) -> device and the per-chain observables come back.
     e2e = None
     if not args.skip_e2e:
-        ctx = bd.Context(Nc, h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, precision=prec)
+        ctx = bd.Context(Nc, precision=prec, **kw)
         ctx.set_state(r0)
         pinned = torch.from_numpy(noise_host).pin_memory()
         obs_host = torch.empty((len(Nc), bd.OBS_STRIDE), dtype=torch.float64).pin_memory()
@@ -200,33 +229,37 @@ def run_ours(args, rank, world, local_rank):
             ctx.step(pinned[W + i:W + i + 1])
             ctx.observables(out=obs_host, with_status=False)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = (time.perf_counter() - t0) * 1e3
         ctx.close()
-        e2e = {"value": len(Nc) * ke * world / el, "unit": UNIT,
-               "h2d_bytes_per_step": total * 3 * 8, "d2h_bytes_per_step": len(Nc) * bd.OBS_STRIDE * 8,
-               "steps": ke}
+        ue, me = replicas.aggregate(el, len(Nc) * ke, world, device=dev)
+        e2e = {"value": ue / (me / 1e3), "unit": UNIT, "h2d_bytes_per_step": total * 3 * 8,
+               "d2h_bytes_per_step": len(Nc) * bd.OBS_STRIDE * 8, "steps": ke}
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        cpu = cpu_baseline(w, Nc, r0.cpu().numpy(), noise_host, args.cpu_chains)
+        cpu = cpu_baseline(w, Nc, r0_host, noise_host, args.cpu_chains)
 
     if rank == 0:
+        tile = 32 if prec == bd.FP64 else 128
+        mat_gb = float(np.sum((np.ceil(n / tile) * tile) ** 2)) * esize / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 storage / tf32 trailing updates / f64 panels and tensions"
-            if prec != bd.FP64 else "f64",
+            "vs_baseline": None,
+            "dtype": "f64" if prec == bd.FP64 else
+                     "f32 storage, tf32 tensor-core products, f32 diagonal tiles, f64-accurate tension solve",
             "data": "synthetic (seeded random-walk chains, N(0,1) noise)",
             "config": {"workload": w.name, "n_chains_per_gpu": len(Nc), "n_beads": int(Nc.max()),
-                       "hstar": w.hstar, "dt": w.dt, "flow": ["none", "shear", "uniaxial"][w.flow],
-                       "Wi": w.Wi, "lambda": 1.0, "precision": "mixed_tf32" if prec else "fp64",
-                       "l2": "inputs larger than L2 (per-step matrices %.1f GB)" %
-                             (float(np.sum((np.ceil(3 * Nc / (128 if prec else 32)) *
-                                            (128 if prec else 32)) ** 2)) * (4 if prec else 8) / 1e9),
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof, "fp64": fp64, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary(), "cpu_baseline": cpu,
-            "chain_status_ok": bool((st == 0).all()),
+                       "hstar": w.hstar, "a": w.hstar, "dt": w.dt,
+                       "flow": ["none", "shear", "uniaxial"][w.flow], "Wi": w.Wi, "lambda": 1.0,
+                       "newton_tol": args.tol,
+                       "precision": "fp64" if prec == bd.FP64 else "mixed_tf32_refined",
+                       "l2": f"inputs larger than L2 (per-step matrices {mat_gb:.1f} GB)",
+                       "parallelism": f"independent replicas x{world}"},
+            "roofline": roof, "rooflines_other": others, "stages": stage, "fp64": fp64,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "cpu_baseline": cpu, "chain_status_ok": bool((st == 0).all()),
+            "max_rod_length_error": float(obs[:, bd.binding.OBS_STRIDE - 2].max().item()),
         }
         print(json.dumps(line))
 
@@ -250,14 +283,14 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle as orc
-    w = workload_cfg(args)
+    w = inputs.WORKLOADS[args.workload]
     Nc = w.lengths()
     cores = orc.num_threads()
     S = int(min(len(Nc), max(1, min(cores, args.cpu_chains))))
     Ns = Nc[:S]
     r = inputs.random_walk(Ns, w.seed)
     noise = inputs.gaussian_noise(args.steps + args.warmup, int(Ns.sum()), w.seed + 1)
-    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi)
+    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol)
     for i in range(args.warmup):
         r, *_ = orc.run(p, Ns, r, noise[i:i + 1])
     t0 = time.perf_counter()
@@ -270,7 +303,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random-walk chains, N(0,1) noise)",
             "config": {"workload": w.name, "n_chains_sampled": S, "n_beads": int(Nc.max()),
-                       "hstar": w.hstar, "dt": w.dt, "Wi": w.Wi},
+                       "hstar": w.hstar, "dt": w.dt, "Wi": w.Wi, "newton_tol": args.tol},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": min(cores, S), "kind": "oracle",
                              "sample": f"{S} of {len(Nc)} chains per step, FP64 CPU oracle"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -280,10 +313,12 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n1000x64_mixed_shear", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32"])
+    ap.add_argument("--tol", type=float, default=1e-13)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-chains", type=int, default=16)
@@ -293,9 +328,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local_rank = replicas.rank_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

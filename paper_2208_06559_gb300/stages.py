@@ -1,0 +1,102 @@
+"""Stage timing and profiling driver for libbd.
+
+    python -m paper_2208_06559_gb300.stages --chains 64 --beads 1000 --precision tf32 [--reps 3]
+
+Creates one context on cuda:0 with seeded random-walk chains, then times each
+stage of the time step through the C ABI with CUDA events on the launching
+stream (assembly, Cholesky factorisation, Brownian displacement, mobility
+product, one full step) and prints one JSON line.  ``--once`` runs every
+stage exactly once without timing (a short, fixed launch sequence for
+kernel profilers).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    import paper_2208_06559_gb300 as bd
+    from paper_2208_06559_gb300 import inputs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--beads", type=int, default=1000)
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "tf32"])
+    ap.add_argument("--flow", type=int, default=1)
+    ap.add_argument("--Wi", type=float, default=100.0)
+    ap.add_argument("--dt", type=float, default=1e-4)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--once", action="store_true")
+    a = ap.parse_args()
+
+    prec = bd.FP64 if a.precision == "fp64" else bd.MIXED_TF32
+    Nc = np.full(a.chains, a.beads, np.int32)
+    r0 = torch.from_numpy(inputs.random_walk(Nc, a.seed)).cuda()
+    ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec)
+    ctx.set_state(r0)
+    xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 3, int(Nc.sum()), a.seed + 1)).cuda()
+    if a.once:
+        ctx.assemble()
+        ctx.factor()
+        ctx.brownian(xi[0])
+        ctx.mobility_apply(xi[1])
+        ctx.step(xi[2:3])
+        torch.cuda.synchronize()
+        st, _ = ctx.chain_status()
+        print(json.dumps({"ok": bool((st == 0).all())}))
+        return
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    res = {}
+
+    def timeit(name, fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(a.reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / a.reps
+
+    timeit("assemble_ms", ctx.assemble)
+    ts = []
+    for _ in range(a.reps):
+        ctx.assemble()
+        e0, e1 = ev(), ev()
+        e0.record()
+        ctx.factor()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    res["factor_ms"] = sum(ts) / len(ts)
+    timeit("brownian_ms", lambda: ctx.brownian(xi[0]))
+    timeit("mobility_ms", lambda: ctx.mobility_apply(xi[1]))
+    ctx.step(xi[0:1])
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    ctx.step(xi[1:1 + a.reps])
+    e1.record()
+    torch.cuda.synchronize()
+    res["step_ms"] = e0.elapsed_time(e1) / a.reps
+    st, it = ctx.chain_status()
+    n = 3.0 * Nc
+    res["factor_tflops"] = float(np.sum(n ** 3) / 3) / (res["factor_ms"] * 1e-3) / 1e12
+    res["newton_iterations"] = int(it.max())
+    res["status_ok"] = bool((st == 0).all())
+    print(json.dumps({"chains": a.chains, "beads": a.beads, "precision": a.precision,
+                      **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in res.items()}}))
+
+
+if __name__ == "__main__":
+    main()
