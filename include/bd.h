@@ -152,6 +152,22 @@ int bd_mobility_apply(bd_ctx* ctx, const double* f_dev, double* u_dev, void* str
 /* Stage 5 input/outputs: tensions of the last step, [sum (N-1)] FP64. */
 int bd_get_tensions(bd_ctx* ctx, double* T_dev, void* stream);
 
+/* Pathwise gradient of an objective J(r_final) with respect to the
+ * Weissenberg number and h*, at fixed noise (the paper has no derivatives).
+ * Runs n_steps FP64 steps from r0_dev [sum N][3] (device) with noise_dev
+ * [n_steps][sum N][3] (device) and returns grad_host[0] = dJ/dWi,
+ * grad_host[1] = dJ/dh* (a = h* when the context was created with a <= 0, so
+ * a moves with h*), given dJdr_final_dev = dJ/dr at the final positions
+ * [sum N][3] (device).  The derivative of the discrete step map is exact: it
+ * is propagated forward (tangents of the RPY assembly, of the Cholesky factor
+ * L' = L Phi(L^{-1} D' L^{-T}), of the Brownian and flow terms, and of the
+ * tension solve by the implicit function theorem), which for two parameters
+ * needs no checkpoints; ckpt_every is accepted and ignored.  The context is
+ * left at the final state.  FP64 contexts with h* > 0 only (else BD_ERR_ARG).
+ * Synchronises the stream; returns the most severe chain status. */
+int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noise_dev,
+               int ckpt_every, const double* dJdr_final_dev, double grad_host[2], void* stream);
+
 /* Copy chain `chain`'s dense n x n (n = 3 N_c) matrix `which` to host FP64
  * row-major: which = 0 -> D, 1 -> the Cholesky factor B (zeros above the
  * diagonal).  Synchronises the legacy default stream. */

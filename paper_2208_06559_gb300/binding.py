@@ -75,6 +75,9 @@ EXPORTS = {
     "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bd_kernel_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.c_void_p]),
+    "bd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_void_p]),
     "bd_mobility_apply_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
@@ -224,6 +227,16 @@ class Context:
                "bd_kernel_launches")
         return int(v.value)
 
+    def adjoint(self, r0, noise, dJdr_final, ckpt_every: int = 20, stream=None):
+        """(dJ/dWi, dJ/dh*) at fixed noise for J with gradient dJdr_final at the
+        final positions; the context ends at the final state."""
+        g = (ctypes.c_double * 2)()
+        rc = lib().bd_adjoint(self._h, _ptr(r0), int(noise.shape[0]), _ptr(noise), int(ckpt_every),
+                              _ptr(dJdr_final), g, _stream(stream))
+        if rc not in (BD_OK,):
+            _check(rc, "bd_adjoint")
+        return float(g[0]), float(g[1])
+
     def factor_residual(self, chain: int) -> float:
         v = ctypes.c_double()
         _check(lib().bd_factor_residual(self._h, int(chain), ctypes.byref(v)), "bd_factor_residual")
@@ -263,3 +276,41 @@ class Context:
         _check(lib().bd_read_matrix(self._h, int(chain), int(which),
                                     out.ctypes.data_as(ctypes.c_void_p)), "bd_read_matrix")
         return out
+
+
+def simulate(Wi, h_star, n_beads, r0, noise, dt: float = 1e-4, flow: int = FLOW_UNIAXIAL,
+             lam: float = 1.0, tol: float = 1e-13, max_newton: int = 50, ckpt_every: int = 20):
+    """Final positions after noise.shape[0] FP64 steps from r0, differentiable
+    with respect to the 0-dim float64 tensors Wi and h_star (a = h_star).
+
+    The backward pass calls bd_adjoint with the incoming gradient at the final
+    positions; the noise is held fixed (pathwise derivative)."""
+    import torch
+
+    class _Run(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx_, wi, hs):
+            c = Context(n_beads, h_star=float(hs), dt=dt, flow=flow, Wi=float(wi), lam=lam, tol=tol,
+                        max_newton=max_newton)
+            c.set_state(r0)
+            c.step(noise)
+            out = c.get_state()
+            torch.cuda.synchronize()
+            st, _ = c.chain_status()
+            c.close()
+            if (st != BD_OK).any():
+                raise BDError(int(st.min()), "simulate")
+            ctx_.save_for_backward(wi, hs)
+            return out
+
+        @staticmethod
+        def backward(ctx_, grad_out):
+            wi, hs = ctx_.saved_tensors
+            c = Context(n_beads, h_star=float(hs), dt=dt, flow=flow, Wi=float(wi), lam=lam, tol=tol,
+                        max_newton=max_newton)
+            gw, gh = c.adjoint(r0, noise, grad_out.contiguous(), ckpt_every)
+            c.close()
+            return (torch.tensor(gw, dtype=wi.dtype, device=wi.device),
+                    torch.tensor(gh, dtype=hs.dtype, device=hs.device))
+
+    return _Run.apply(Wi, h_star)

@@ -137,6 +137,32 @@ cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const
                            const ChainDesc* cd, int n_chains, int max_tiles, int* status,
                            cudaStream_t s);
 
+// Forward-mode tangents of the FP64 step (k_tangent.cu).
+cudaError_t launch_assemble_dot(const double* r, const double* rdot, const ChainDesc* cd, int n_chains,
+                                int max_N, double* Md, double hstar, double a, double hdot,
+                                double adot, cudaStream_t s);
+cudaError_t launch_trsm_rhs(const double* M, const double* Winv, const ChainDesc* cd, int n_chains,
+                            int max_tiles, double* B, cudaStream_t s);
+cudaError_t launch_transpose(const ChainDesc* cd, int n_chains, int max_tiles, double* B,
+                             cudaStream_t s);
+cudaError_t launch_phi_matvec(const double* X, const ChainDesc* cd, int n_chains, int max_n,
+                              const double* xi, double* v, cudaStream_t s);
+cudaError_t launch_gemv_dense(const double* A, const ChainDesc* cd, int n_chains, int max_n,
+                              const double* f, double* w, cudaStream_t s);
+cudaError_t launch_tangent_predictor(const double* r, const double* rdot, const double* ydot,
+                                     const double* uhat, const double* T, const ChainDesc* cd,
+                                     int n_chains, int max_N, Phys ph, const double* kappa_dot,
+                                     double* rsdot, double* G, cudaStream_t s);
+cudaError_t launch_tangent_base(const ChainDesc* cd, int n_chains, int max_n, Phys ph,
+                                const double* rsdot, const double* DdF, const double* DG, double* a,
+                                cudaStream_t s);
+cudaError_t launch_tangent_residual(const double* a, const double* u, const double* rnew,
+                                    const ChainDesc* cd, int n_chains, Phys ph, double rel_tol,
+                                    double* rscale, double* z, double* rhs, int* state, int* status,
+                                    const int* iters, cudaStream_t s);
+cudaError_t launch_tangent_init(const ChainDesc* cd, int n_chains, int max_n, const int* status,
+                                int* state, int* iters, double* Tdot, double* Fdot, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_extract(const T* M, const ChainDesc* cd, int chain, int which, double* out,
                            cudaStream_t s);

@@ -67,6 +67,10 @@ struct bd_ctx {
   cudaEvent_t aev[4] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // forward-mode tangent workspace (allocated by the first bd_adjoint call)
+  double *Md = nullptr, *rdot = nullptr, *ydot = nullptr, *rsdot = nullptr, *Gt = nullptr;
+  double *abase = nullptr, *zt = nullptr, *DdF = nullptr, *DG = nullptr, *vt = nullptr;
+  double *Tdot = nullptr, *Fdot = nullptr, *rscale = nullptr, *kdot = nullptr;
   bool have_state = false;
   int direct_iters = 0;  // > 0: launch the step's kernels directly (profiling), no graph
   std::mutex mu;
@@ -387,7 +391,8 @@ void bd_destroy(bd_ctx* c) {
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
                   c->stage, c->status, c->state, c->iters, c->args, c->loops, c->Winv, c->tmaps,
-                  c->Minv, c->Kinv};
+                  c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
+                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
@@ -713,6 +718,119 @@ int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
     CK(cudaMemcpyAsync(T_dev, c->T, (size_t)c->total_rods * sizeof(double), cudaMemcpyDefault,
                        (cudaStream_t)stream));
   return BD_OK;
+}
+
+int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
+               const double* dJdr_final_dev, double grad_host[2], void* stream) {
+  (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
+  if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
+  if (c->mixed || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b3 = (size_t)c->total_beads * 3;
+  const size_t nr = (size_t)(c->total_rods > 0 ? c->total_rods : 1);
+  if (!c->Md) {
+    auto al = [&](double** p, size_t n) {
+      if (cudaMalloc(p, (n < 2 ? 2 : n) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return true;
+    };
+    if (!(al(&c->Md, c->M_elems) && al(&c->rdot, 2 * b3) && al(&c->ydot, b3) && al(&c->rsdot, b3) &&
+          al(&c->Gt, b3) && al(&c->abase, b3) && al(&c->zt, b3) && al(&c->DdF, b3) && al(&c->DG, b3) &&
+          al(&c->vt, b3) && al(&c->Tdot, nr) && al(&c->Fdot, b3) && al(&c->rscale, c->n_chains) &&
+          al(&c->kdot, 18)))
+      return BD_ERR_OOM;
+    CK(cudaMemsetAsync(c->Md, 0, c->M_elems * sizeof(double), s));
+  }
+  // d kappa / d Wi = kappa at rate 1 / lambda; d kappa / d h* = 0
+  double kd[18] = {0};
+  const double lam = c->p.lambda > 0.0 ? c->p.lambda : 1.0;
+  if (c->p.flow == BD_FLOW_UNIAXIAL) {
+    kd[0] = 1.0 / lam;
+    kd[4] = -0.5 / lam;
+    kd[8] = -0.5 / lam;
+  } else if (c->p.flow == BD_FLOW_SHEAR) {
+    kd[1] = 1.0 / lam;
+  }
+  CK(cudaMemcpyAsync(c->kdot, kd, sizeof(kd), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->r, r0_dev, b3 * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int) * c->n_chains, s));
+  CK(cudaMemsetAsync(c->rdot, 0, 2 * b3 * sizeof(double), s));
+  c->have_state = true;
+  const bool tied = !(c->p.a > 0.0);  // a = h*: a moves with h*
+  const int tiles = c->max_np / kSimtTile;
+  const int iters_max = c->ph.max_newton + 2;
+  int rc;
+  for (int step = 0; step < n_steps; ++step) {
+    const double* xi = noise_dev + (size_t)step * b3;
+    // ---- primal step, intermediates kept (r still holds the old positions)
+    if ((rc = enqueue_assemble(c, s))) return rc;
+    if ((rc = enqueue_factor(c, s))) return rc;
+    CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, xi, nullptr, c->ph.sq2dt,
+                           c->y, s));
+    CK(launch_rod_dirs(c->r, c->d_cd, c->n_chains, c->max_N, c->uhat, s));
+    CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
+                             c->uhat, s));
+    CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
+                                c->max_mp / kSimtTile, true, c->status, s));
+    CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
+                        c->F, c->state, c->status, c->iters, s));
+    for (int it = 0; it < iters_max; ++it) {
+      if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+      CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
+                                c->status, c->iters, s));
+      CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
+                                     c->ph, c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
+    }
+    // ---- tangents for p = Wi (0) and p = h* (1)
+    for (int p = 0; p < 2; ++p) {
+      double* rd = c->rdot + (size_t)p * b3;
+      const double hdot = (p == 1) ? 1.0 : 0.0, adot = (p == 1 && tied) ? 1.0 : 0.0;
+      CK(launch_assemble_dot(c->r, rd, c->d_cd, c->n_chains, c->max_N, c->Md, c->ph.hstar, c->ph.a, hdot,
+                             adot, s));
+      CK(launch_gemv_dense(c->Md, c->d_cd, c->n_chains, c->max_n, c->F, c->DdF, s));
+      CK(launch_trsm_rhs((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, tiles, c->Md,
+                         s));
+      CK(launch_transpose(c->d_cd, c->n_chains, tiles, c->Md, s));
+      CK(launch_trsm_rhs((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, tiles, c->Md,
+                         s));
+      CK(launch_phi_matvec(c->Md, c->d_cd, c->n_chains, c->max_n, xi, c->vt, s));
+      CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, c->vt, nullptr,
+                             c->ph.sq2dt, c->ydot, s));
+      CK(launch_tangent_predictor(c->r, rd, c->ydot, c->uhat, c->T, c->d_cd, c->n_chains, c->max_N, c->ph,
+                                  c->kdot + 9 * p, c->rsdot, c->Gt, s));
+      if ((rc = enqueue_symv(c, c->Gt, c->DG, nullptr, s))) return rc;
+      CK(launch_tangent_base(c->d_cd, c->n_chains, c->max_n, c->ph, c->rsdot, c->DdF, c->DG, c->abase, s));
+      CK(launch_tangent_init(c->d_cd, c->n_chains, c->max_n, c->status, c->state, c->iters, c->Tdot,
+                             c->Fdot, s));
+      for (int it = 0; it < iters_max; ++it) {
+        if ((rc = enqueue_symv(c, c->Fdot, c->u, c->state, s))) return rc;
+        CK(launch_tangent_residual(c->abase, c->u, c->rT, c->d_cd, c->n_chains, c->ph, 1e-12, c->rscale,
+                                   c->zt, c->rhs, c->state, c->status, c->iters, s));
+        CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
+                                       c->ph, c->uhat, c->rhs, c->Tdot, c->Fdot, c->state, c->iters, s));
+      }
+      CK(cudaMemcpyAsync(rd, c->zt, b3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    // ---- commit the primal step
+    CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status, nullptr,
+                       s));
+  }
+  std::vector<double> J(b3), rd(2 * b3);
+  CK(cudaMemcpyAsync(J.data(), dJdr_final_dev, b3 * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(rd.data(), c->rdot, 2 * b3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<int> st(c->n_chains);
+  CK(cudaMemcpyAsync(st.data(), c->status, sizeof(int) * c->n_chains, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int p = 0; p < 2; ++p) {
+    long double acc = 0.0L;
+    for (size_t e = 0; e < b3; ++e) acc += (long double)J[e] * (long double)rd[(size_t)p * b3 + e];
+    grad_host[p] = (double)acc;
+  }
+  return worst(st.data(), c->n_chains);
 }
 
 int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
