@@ -125,9 +125,14 @@ def run_ours(args, rank, world, local_rank):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
+    tuned = {}
+
     def timed_steps(p, nsteps, nwarm):
         ctx = bd.Context(Nc, precision=p, **kw)
         ctx.set_state(r0)
+        if p != bd.FP64 and not args.no_tune:   # tile shapes of the tensor-core factorisation
+            pan, grp, tms = ctx.tune_factor()
+            tuned.update(panel=pan, groups=grp, tuned_factor_ms=tms)
         for i in range(nwarm):
             ctx.step(noise[i:i + 1])
         barrier()
@@ -218,6 +223,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_e2e:
         ctx = bd.Context(Nc, precision=prec, **kw)
         ctx.set_state(r0)
+        if tuned.get("panel"):
+            bd.lib().bd_set_factor_config(ctx._h, tuned["panel"], tuned["groups"])
         pinned = torch.from_numpy(noise_host).pin_memory()
         obs_host = torch.empty((len(Nc), bd.OBS_STRIDE), dtype=torch.float64).pin_memory()
         ctx.step(pinned[0:1])
@@ -256,7 +263,8 @@ def run_ours(args, rank, world, local_rank):
                        "precision": "fp64" if prec == bd.FP64 else "mixed_tf32_refined",
                        "l2": f"inputs larger than L2 (per-step matrices {mat_gb:.1f} GB)",
                        "parallelism": f"independent replicas x{world}"},
-            "roofline": roof, "rooflines_other": others, "stages": stage, "fp64": fp64,
+            "roofline": roof, "rooflines_other": others, "stages": stage, "factor_shape": tuned,
+            "fp64": fp64,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
             "cpu_baseline": cpu, "chain_status_ok": bool((st == 0).all()),
             "max_rod_length_error": float(obs[:, bd.binding.OBS_STRIDE - 2].max().item()),
@@ -325,6 +333,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -78,6 +78,10 @@ EXPORTS = {
     "bd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_void_p]),
+    "bd_tune_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_void_p]),
+    "bd_set_factor_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bd_mobility_apply_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
@@ -236,6 +240,33 @@ class Context:
         if rc not in (BD_OK,):
             _check(rc, "bd_adjoint")
         return float(g[0]), float(g[1])
+
+    def tune_factor(self, cache_path: Optional[str] = None, stream=None):
+        """Pick the mixed factorisation's super-panel width and chain-group
+        count by timing (bd_tune_factor), or reuse the entry of a JSON cache
+        keyed by the padded order, chain count and precision.  Returns
+        (panel, groups, ms) (ms is None for a cached entry)."""
+        import json
+        n_pad = int(-(-3 * int(self.n_beads.max()) // 128) * 128)
+        key = f"prec{self.precision}:np{n_pad}:chains{self.n_chains}"
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        if key in cache:
+            p, g = cache[key]["panel"], cache[key]["groups"]
+            _check(lib().bd_set_factor_config(self._h, int(p), int(g)), "bd_set_factor_config")
+            return p, g, None
+        p, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().bd_tune_factor(self._h, ctypes.byref(p), ctypes.byref(g), ctypes.byref(ms),
+                                    _stream(stream)), "bd_tune_factor")
+        if cache_path:
+            cache[key] = {"panel": p.value, "groups": g.value, "ms": ms.value}
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache_path)
+        return p.value, g.value, ms.value
 
     def factor_residual(self, chain: int) -> float:
         v = ctypes.c_double()

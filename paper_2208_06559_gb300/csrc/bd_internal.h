@@ -117,6 +117,7 @@ cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_ch
 
 // Opt-in shared-memory sizes of the matvec kernels (once per device).
 cudaError_t matvec_configure();
+cudaError_t assemble_configure();
 cudaError_t tension_configure();
 
 // Mixed-precision Brownian displacement with one refinement step (k_refine.cu):
@@ -134,7 +135,7 @@ cudaError_t tc_configure();
 // Factor chains [0, n_chains) of the given arrays (pointers may be offset to
 // a chain subrange); wmap is the TMA map of Winv.
 cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
-                           const ChainDesc* cd, int n_chains, int max_tiles, int* status,
+                           const ChainDesc* cd, int n_chains, int max_tiles, int panel, int* status,
                            cudaStream_t s);
 
 // Forward-mode tangents of the FP64 step (k_tangent.cu).

@@ -56,8 +56,9 @@ struct bd_ctx {
   cudaStream_t cs = nullptr, cs2 = nullptr;
   // mixed factorisation: chain groups on their own streams, so that one
   // group's latency-bound diagonal-tile step overlaps another's products
-  static constexpr int kMaxGroups = 4;
+  static constexpr int kMaxGroups = 8;
   int n_groups = 1;
+  int panel = 4;                     // super-panel width of the mixed factorisation (tiles)
   std::vector<int> group_start;      // chain index of each group's first chain (+ end)
   std::vector<int> group_tiles;      // max 128-tiles of each group
   cudaStream_t gs[kMaxGroups] = {};
@@ -104,7 +105,7 @@ int enqueue_factor(bd_ctx* c, cudaStream_t s) {
     const CUtensorMap* wmap = c->tmaps + c->n_chains;
     if (c->n_groups <= 1) {
       CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps, wmap, c->d_cd, c->n_chains,
-                        c->max_np / kMixedTile, c->status, s));
+                        c->max_np / kMixedTile, c->panel, c->status, s));
       return BD_OK;
     }
     // fork
@@ -113,7 +114,7 @@ int enqueue_factor(bd_ctx* c, cudaStream_t s) {
       CK(cudaStreamWaitEvent(c->gs[g], c->gev[c->kMaxGroups], 0));
       const int c0 = c->group_start[g], c1 = c->group_start[g + 1];
       CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps + c0, wmap, c->d_cd + c0, c1 - c0,
-                        c->group_tiles[g], c->status + c0, c->gs[g]));
+                        c->group_tiles[g], c->panel, c->status + c0, c->gs[g]));
       CK(cudaEventRecord(c->gev[g], c->gs[g]));
     }
     // join
@@ -286,6 +287,27 @@ int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
   CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
                      c->args, s));
   return BD_OK;
+}
+
+// Split the chains into G groups (each factored on its own stream).
+void set_groups(bd_ctx* c, int G) {
+  if (G < 1) G = 1;
+  if (G > bd_ctx::kMaxGroups) G = bd_ctx::kMaxGroups;
+  if (G > c->n_chains) G = c->n_chains;
+  c->n_groups = G;
+  c->group_start.assign(G + 1, 0);
+  c->group_tiles.assign(G, 0);
+  for (int g = 0; g <= G; ++g) c->group_start[g] = (int)((long long)c->n_chains * g / G);
+  for (int g = 0; g < G; ++g)
+    for (int i = c->group_start[g]; i < c->group_start[g + 1]; ++i)
+      if (c->h_cd[i].np / kMixedTile > c->group_tiles[g]) c->group_tiles[g] = c->h_cd[i].np / kMixedTile;
+}
+
+void drop_graph(bd_ctx* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->exec = nullptr;
+  c->graph = nullptr;
 }
 
 bool is_device_ptr(const void* p) {
@@ -542,24 +564,13 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       return fail(BD_ERR_CUDA);
   cudaStream_t s = c->cs;
   if (c->mixed) {
-    c->n_groups = c->n_chains / 16;
-    if (c->n_groups < 1) c->n_groups = 1;
-    if (c->n_groups > bd_ctx::kMaxGroups) c->n_groups = bd_ctx::kMaxGroups;
-    c->group_start.assign(c->n_groups + 1, 0);
-    c->group_tiles.assign(c->n_groups, 0);
-    for (int g = 0; g <= c->n_groups; ++g)
-      c->group_start[g] = (int)((long long)c->n_chains * g / c->n_groups);
-    for (int g = 0; g < c->n_groups; ++g)
-      for (int i = c->group_start[g]; i < c->group_start[g + 1]; ++i)
-        if (c->h_cd[i].np / kMixedTile > c->group_tiles[g]) c->group_tiles[g] = c->h_cd[i].np / kMixedTile;
-    if (c->n_groups > 1) {
-      for (int g = 0; g < c->n_groups; ++g)
-        if (cudaStreamCreateWithFlags(&c->gs[g], cudaStreamNonBlocking) != cudaSuccess)
-          return fail(BD_ERR_CUDA);
-      for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
-        if (cudaEventCreateWithFlags(&c->gev[g], cudaEventDisableTiming) != cudaSuccess)
-          return fail(BD_ERR_CUDA);
-    }
+    set_groups(c, c->n_chains / 16);
+    for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
+      if (cudaStreamCreateWithFlags(&c->gs[g], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(BD_ERR_CUDA);
+    for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
+      if (cudaEventCreateWithFlags(&c->gev[g], cudaEventDisableTiming) != cudaSuccess)
+        return fail(BD_ERR_CUDA);
     std::vector<CUtensorMap> hm(c->n_chains + 1);
     if (!make_tc_maps(hm.data(), (float*)c->M, c->Winv, c->h_cd.data(), c->n_chains))
       return fail(BD_ERR_CUDA);
@@ -569,6 +580,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       return fail(BD_ERR_CUDA);
   }
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
+      assemble_configure() != cudaSuccess ||
       k64_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
@@ -831,6 +843,64 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
     grad_host[p] = (double)acc;
   }
   return worst(st.data(), c->n_chains);
+}
+
+int bd_set_factor_config(bd_ctx* c, int panel, int groups) {
+  if (!c || !c->mixed || panel < 1 || panel > 16 || groups < 1 || groups > bd_ctx::kMaxGroups)
+    return BD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->panel = panel;
+  set_groups(c, groups);
+  drop_graph(c);
+  return BD_OK;
+}
+
+int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, void* stream) {
+  if (!c || !c->mixed) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int panels[] = {1, 2, 4, 8};
+  const int groups[] = {1, 2, 4, 8};
+  double best = 1e30;
+  int bp = c->panel, bg = c->n_groups;
+  int rc = BD_OK;
+  for (int gi = 0; gi < 4 && rc == BD_OK; ++gi) {
+    if (groups[gi] > c->n_chains) continue;
+    for (int pi = 0; pi < 4 && rc == BD_OK; ++pi) {
+      c->panel = panels[pi];
+      set_groups(c, groups[gi]);
+      float tot = 0.f;
+      for (int rep = 0; rep < 3 && rc == BD_OK; ++rep) {  // first repetition warms up
+        if ((rc = enqueue_assemble(c, s))) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (!rc) rc = enqueue_factor(c, s);
+        if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = BD_ERR_CUDA;
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (rep > 0) tot += ms;
+      }
+      if (!rc && tot / 2 < best) {
+        best = tot / 2;
+        bp = panels[pi];
+        bg = groups[gi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->panel = bp;
+  set_groups(c, bg);
+  drop_graph(c);
+  if (rc) return rc;
+  if (panel_out) *panel_out = bp;
+  if (groups_out) *groups_out = bg;
+  if (ms_out) *ms_out = best;
+  return BD_OK;
 }
 
 int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {

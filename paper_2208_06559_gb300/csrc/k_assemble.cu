@@ -2,9 +2,9 @@
 //
 // The paper's "Diffusion Tensor" kernel (Sec. 4) releases one thread per
 // scalar element of the dense 3(N+1) x 3(N+1) matrix and branches on i == j.
-// Here one thread evaluates one 3x3 bead-pair block (the separation, its norm
+// Here one thread evaluates 3x3 bead-pair blocks (the separation, its norm
 // and the two RPY coefficients are shared by the nine elements), a CTA stages
-// a 16 x 16 bead tile (48 x 48 elements) in shared memory, and the tile is
+// a 32 x 32 bead tile (96 x 96 elements) in shared memory, and the tile is
 // written twice with coalesced row stores: once at (i, j) and once transposed
 // at (j, i).  The result is the full symmetric D in the chain's row-major
 // matrix; the Cholesky later overwrites the lower triangle with the factor and
@@ -13,8 +13,12 @@
 
 namespace bd {
 
-constexpr int kBeadTile = 16;
-constexpr int kElTile = 3 * kBeadTile;
+constexpr int kBeadTile = 32;
+constexpr int kElTile = 3 * kBeadTile;  // 96 x 96 elements per tile
+template <typename T>
+constexpr int assemble_smem() {
+  return kElTile * (kElTile + 1) * (int)sizeof(T);
+}
 
 // Coefficients of D_ij = cI * I + cRR * R R^T for separation R (|R|^2 = R2).
 // Eq. (8) for R >= 2a, Eq. (9) for R < 2a, the overlap limit (h*/a) I at R = 0.
@@ -41,7 +45,8 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
                                                   const ChainDesc* __restrict__ cd, double hstar,
                                                   double a) {
   using C = T;  // arithmetic type of the coefficients (FP64 or FP32)
-  __shared__ T S[kElTile][kElTile + 1];
+  extern __shared__ __align__(16) uint8_t as_smem[];
+  T (*S)[kElTile + 1] = reinterpret_cast<T (*)[kElTile + 1]>(as_smem);
   const ChainDesc d = cd[blockIdx.y];
   const int TB = (d.N + kBeadTile - 1) / kBeadTile;
   const int p = blockIdx.x;
@@ -51,32 +56,36 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
   while ((bi + 1) * (bi + 2) / 2 <= p) ++bi;
   const int bj = p - bi * (bi + 1) / 2;  // bj <= bi
 
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = bi * kBeadTile + ty, j = bj * kBeadTile + tx;
-  T blk[9];
+  // 1024 bead pairs per tile, four per thread
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    const int ty = e >> 5, tx = e & 31;
+    const int i = bi * kBeadTile + ty, j = bj * kBeadTile + tx;
+    T blk[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) blk[q] = T(0);
-  if (i < d.N && j < d.N) {
-    if (i == j) {
-      blk[0] = blk[4] = blk[8] = T(1);
-    } else {
-      const double* ri = r + 3 * (d.boff + i);
-      const double* rj = r + 3 * (d.boff + j);
-      const double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
-      const C R[3] = {(C)dx, (C)dy, (C)dz};
-      const C R2 = (C)(dx * dx + dy * dy + dz * dz);
-      C cI, cRR;
-      rpy_coeffs<C>(R2, (C)hstar, (C)a, cI, cRR);
+    for (int w = 0; w < 9; ++w) blk[w] = T(0);
+    if (i < d.N && j < d.N) {
+      if (i == j) {
+        blk[0] = blk[4] = blk[8] = T(1);
+      } else {
+        const double* ri = r + 3 * (d.boff + i);
+        const double* rj = r + 3 * (d.boff + j);
+        const double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
+        const C R[3] = {(C)dx, (C)dy, (C)dz};
+        const C R2 = (C)(dx * dx + dy * dy + dz * dz);
+        C cI, cRR;
+        rpy_coeffs<C>(R2, (C)hstar, (C)a, cI, cRR);
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int l = 0; l < 3; ++l) blk[3 * k + l] = (k == l ? cI : C(0)) + cRR * R[k] * R[l];
+          for (int l = 0; l < 3; ++l) blk[3 * k + l] = (k == l ? cI : C(0)) + cRR * R[k] * R[l];
+      }
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) S[3 * ty + k][3 * tx + l] = blk[3 * k + l];
   }
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int l = 0; l < 3; ++l) S[3 * ty + k][3 * tx + l] = blk[3 * k + l];
   __syncthreads();
 
   T* base = M + d.moff;
@@ -101,7 +110,7 @@ cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_ch
                             double hstar, double a, cudaStream_t s) {
   const int TB = (max_N + kBeadTile - 1) / kBeadTile;
   dim3 grid(TB * (TB + 1) / 2, n_chains);
-  k_assemble<T><<<grid, 256, 0, s>>>(r, M, cd, hstar, a);
+  k_assemble<T><<<grid, 256, assemble_smem<T>(), s>>>(r, M, cd, hstar, a);
   return cudaGetLastError();
 }
 
@@ -162,5 +171,14 @@ template cudaError_t launch_extract<double>(const double*, const ChainDesc*, int
                                             cudaStream_t);
 template cudaError_t launch_extract<float>(const float*, const ChainDesc*, int, int, double*,
                                            cudaStream_t);
+
+cudaError_t assemble_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       assemble_smem<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             assemble_smem<float>());
+  return e;
+}
 
 }  // namespace bd

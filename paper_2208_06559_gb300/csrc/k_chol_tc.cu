@@ -306,13 +306,11 @@ cudaError_t tc_configure() {
   return e;
 }
 
-// Right-looking with super-panels of kPanel tile columns: inside a panel,
+// Right-looking with super-panels of `panel` tile columns: inside a panel,
 // column k first receives the updates of the panel's earlier columns
 // (K = 128 (k - K0)), is factored and solved; the trailing matrix is updated
-// once per panel with K = 128 kPanel, so every trailing tile is read and
-// written kPanel times less often than with single-column steps.
-constexpr int kPanel = 4;
-
+// once per panel with K = 128 panel, so every trailing tile is read and
+// written `panel` times less often than with single-column steps.
 static int update_tiles(int T, int j0, int j1) {
   int n = 0;
   for (int j = j0; j < j1 && j < T; ++j) n += T - j;
@@ -320,11 +318,12 @@ static int update_tiles(int T, int j0, int j1) {
 }
 
 cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
-                           const ChainDesc* cd, int n_chains, int max_tiles, int* status,
+                           const ChainDesc* cd, int n_chains, int max_tiles, int panel, int* status,
                            cudaStream_t s) {
   const int T = max_tiles;
-  for (int K0 = 0; K0 < T; K0 += kPanel) {
-    const int K1 = K0 + kPanel < T ? K0 + kPanel : T;
+  if (panel < 1) panel = 1;
+  for (int K0 = 0; K0 < T; K0 += panel) {
+    const int K1 = K0 + panel < T ? K0 + panel : T;
     for (int k = K0; k < K1; ++k) {
       if (k > K0)
         k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, k, k + 1), n_chains), 128, kTcSmem, s>>>(

@@ -68,7 +68,16 @@ __global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
     if (row >= d.n) return;
     const float* Lr = base + (long long)row * d.np;
     DFa acc{0.f, 0.f};
-    for (int c = lane; c <= row; c += 32) dfa_add_prod(acc, Lr[c], xh[c], xl[c]);
+    int c = lane;
+    for (; c + 96 <= row; c += 128) {  // four loads in flight per lane
+      const float v0 = __ldg(Lr + c), v1 = __ldg(Lr + c + 32), v2 = __ldg(Lr + c + 64),
+                  v3 = __ldg(Lr + c + 96);
+      dfa_add_prod(acc, v0, xh[c], xl[c]);
+      dfa_add_prod(acc, v1, xh[c + 32], xl[c + 32]);
+      dfa_add_prod(acc, v2, xh[c + 64], xl[c + 64]);
+      dfa_add_prod(acc, v3, xh[c + 96], xl[c + 96]);
+    }
+    for (; c <= row; c += 32) dfa_add_prod(acc, Lr[c], xh[c], xl[c]);
     const double t = dwarp_sum((double)acc.hi + (double)acc.lo);
     if (lane == 0) y[3 * d.boff + row] = scale * t;
   }
@@ -135,8 +144,14 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __rest
       if (a < c0) {
         const float* col = base + (long long)c0 * np + a;
         DFa s = acc[q];
-#pragma unroll 4
-        for (int rho = 0; rho < 128; ++rho) dfa_add_prod(s, col[rho * np], zh[rho], zl[rho]);
+        // 16 independent loads in flight before the dependent accumulation
+        for (int r0 = 0; r0 < 128; r0 += 16) {
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = __ldg(col + (long long)(r0 + j) * np);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) dfa_add_prod(s, v[j], zh[r0 + j], zl[r0 + j]);
+        }
         acc[q] = s;
       }
     }

@@ -126,3 +126,30 @@ def test_mixed_without_refinement_is_plain_factor(bd):
     yref = np.sqrt(2e-4) * Lt @ xi.ravel()
     assert np.abs(y - yref).max() / np.abs(yref).max() < 1e-9
     ctx.close()
+
+
+def test_factor_tuning_and_configs(bd, tmp_path):
+    """Every (panel, groups) shape gives a valid factor; the tuner picks one of
+    them, writes the cache, and a cached entry is reused."""
+    Nc = np.array([300] * 6 + [200, 43], np.int32)
+    r0 = inputs.random_walk(Nc, 41)
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32)
+    ctx.set_state(cuda(r0))
+    L = bd.lib()
+    for panel in (1, 2, 4, 8):
+        for groups in (1, 2, 4, 8):
+            assert L.bd_set_factor_config(ctx._h, panel, groups) == 0
+            ctx.assemble()
+            ctx.factor()
+            st, _ = ctx.chain_status()
+            assert (st == 0).all()
+            assert max(ctx.factor_residual(c) for c in (0, 6, 7)) < 2e-3
+    cache = str(tmp_path / "tune.json")
+    p, g, ms = ctx.tune_factor(cache)
+    assert p in (1, 2, 4, 8) and g in (1, 2, 4, 8) and ms > 0
+    p2, g2, ms2 = ctx.tune_factor(cache)
+    assert (p2, g2, ms2) == (p, g, None)
+    ctx.step(cuda(inputs.gaussian_noise(2, int(Nc.sum()), 42)))
+    obs, st = ctx.observables()
+    assert (st == 0).all() and obs[:, 6].max().item() < 1e-10
+    ctx.close()
