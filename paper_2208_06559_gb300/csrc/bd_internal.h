@@ -81,6 +81,10 @@ template <typename T>
 cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_np,
                         const double* f, double* scratch, double* u, const int* state,
                         cudaStream_t s);
+// FP32-storage mobility product with a per-chain accuracy switch (see k_matvec.cu).
+cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
+                            const double* f, double* scratch, double* u, const int* state,
+                            const int* accurate, cudaStream_t s);
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s);
@@ -90,10 +94,12 @@ cudaError_t launch_rod_dirs(const double* r, const ChainDesc* cd, int n_chains, 
 cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd,
                              int n_chains, int max_N, Phys ph, double* rstar,
                              const double* uhat, double* T, double* F, int* state,
-                             const int* status, int* iters, cudaStream_t s);
+                             const int* status, int* iters, int* accurate, cudaStream_t s);
+// `accurate` (may be NULL): per chain, set to 1 once max|g| < 1e-5 (the
+// next mobility product must then be FP64-accurate).
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs,
-                                   int* state, int* status, const int* iters,
+                                   int* state, int* status, const int* iters, int* accurate,
                                    cudaStream_t s);
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,

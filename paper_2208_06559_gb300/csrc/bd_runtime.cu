@@ -49,6 +49,7 @@ struct bd_ctx {
   double* stage = nullptr;  // staging for host-memory noise / observables
   size_t stage_elems = 0;
   int *status = nullptr, *state = nullptr, *iters = nullptr;
+  int* accurate = nullptr;  // mixed: per chain, 1 once the tension residual needs FP64-level sums
   StepArgs* args = nullptr;
   unsigned long long* loops = nullptr;  // Newton loop-body executions (device counter)
   unsigned long long steps_launched = 0;
@@ -185,15 +186,26 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
   CK(cudaStreamWaitEvent(s, c->aev[1], 0));
   CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
-                      c->F, c->state, c->status, c->iters, s));
+                      c->F, c->state, c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
+  return BD_OK;
+}
+
+// Mobility product of the tension iteration: in the mixed path plain FP32
+// sums while a chain's residual is large, compensated (FP64-level) after.
+int enqueue_newton_symv(bd_ctx* c, cudaStream_t s) {
+  if (c->mixed)
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->scratch, c->u,
+                       c->state, c->accurate, s));
+  else
+    return enqueue_symv(c, c->F, c->u, c->state, s);
   return BD_OK;
 }
 
 int enqueue_newton_body(bd_ctx* c, cudaGraphConditionalHandle h, cudaStream_t s) {
   int rc;
-  if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+  if ((rc = enqueue_newton_symv(c, s))) return rc;
   CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                            c->status, c->iters, s));
+                            c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
   if (c->mixed)
     CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
                                   c->T, c->F, c->state, c->iters, s));
@@ -274,9 +286,9 @@ int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
   int rc;
   if ((rc = enqueue_pre_newton(c, s))) return rc;
   for (int it = 0; it < c->direct_iters; ++it) {
-    if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+    if ((rc = enqueue_newton_symv(c, s))) return rc;
     CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                              c->status, c->iters, s));
+                              c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
     if (c->mixed)
       CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
                                     c->T, c->F, c->state, c->iters, s));
@@ -412,7 +424,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->args, c->loops, c->Winv, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -539,6 +551,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
             alloc((void**)&c->status, sizeof(int) * c->n_chains) &&
             alloc((void**)&c->state, sizeof(int) * c->n_chains) &&
             alloc((void**)&c->iters, sizeof(int) * c->n_chains) &&
+            alloc((void**)&c->accurate, sizeof(int) * c->n_chains) &&
             alloc((void**)&c->args, sizeof(StepArgs)) &&
             alloc((void**)&c->loops, sizeof(unsigned long long));
   ok = ok && alloc(&c->Kinv, (size_t)kwrow * 64 * c->elem) &&
@@ -789,11 +802,11 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
     CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
                                 c->max_mp / kSimtTile, true, c->status, s));
     CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
-                        c->F, c->state, c->status, c->iters, s));
+                        c->F, c->state, c->status, c->iters, nullptr, s));
     for (int it = 0; it < iters_max; ++it) {
       if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
       CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                                c->status, c->iters, s));
+                                c->status, c->iters, nullptr, s));
       CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
                                      c->ph, c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
     }

@@ -298,11 +298,15 @@ __device__ __forceinline__ void df_add_prod(DF& a, float d, float fh, float fl) 
 
 constexpr int kSymvF32Smem = (SF * SFP + 4 * SF) * 4;
 
+// `accurate` (per chain, may be NULL = always): 0 selects plain FP32 sums
+// (relative error ~1e-7), used by the tension iteration while its residual
+// is still large.
 __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict__ M,
                                                         const ChainDesc* __restrict__ cd,
                                                         const double* __restrict__ f,
                                                         double* __restrict__ P,
-                                                        const int* __restrict__ state) {
+                                                        const int* __restrict__ state,
+                                                        const int* __restrict__ accurate) {
   __shared__ __align__(16) float S[SF][SFP];
   __shared__ float frh[SF], frl[SF], fch[SF], fcl[SF];
   const int c = blockIdx.y;
@@ -349,6 +353,27 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
   }
   const long long ld = (long long)TSn * SF;
   double* Pc = P + d.soff;
+  if (accurate && accurate[c] == 0) {
+    if (t < SF) {
+      float acc = 0.f;
+#pragma unroll 4
+      for (int q4 = 0; q4 < SF / 4; ++q4) {
+        const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
+        acc = fmaf(v.x, fch[4 * q4], acc);
+        acc = fmaf(v.y, fch[4 * q4 + 1], acc);
+        acc = fmaf(v.z, fch[4 * q4 + 2], acc);
+        acc = fmaf(v.w, fch[4 * q4 + 3], acc);
+      }
+      Pc[bj * ld + r0 + t] = (double)acc;
+    } else if (!diag) {
+      const int q = t - SF;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < SF; ++r) acc = fmaf(S[r][q], frh[r], acc);
+      Pc[bi * ld + c0 + q] = (double)acc;
+    }
+    return;
+  }
   if (t < SF) {
     DF acc{0.f, 0.f};
 #pragma unroll 4
@@ -384,12 +409,23 @@ __global__ void k_symv_reduce_w(const ChainDesc* __restrict__ cd, const double* 
   u[3 * d.boff + row] = s;
 }
 
+cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
+                            const double* f, double* scratch, double* u, const int* state,
+                            const int* accurate, cudaStream_t s) {
+  const int TSn = ceil_div(max_np, SF);
+  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state,
+                                                                        accurate);
+  k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_symv<float>(const float* M, const ChainDesc* cd, int n_chains, int max_np,
                                const double* f, double* scratch, double* u, const int* state,
                                cudaStream_t s) {
   const int TSn = ceil_div(max_np, SF);
-  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state);
+  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state,
+                                                                        nullptr);
   k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
   return cudaGetLastError();
 }

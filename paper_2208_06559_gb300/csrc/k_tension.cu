@@ -89,13 +89,14 @@ __global__ void k_predictor(const double* __restrict__ r, const double* __restri
                             double* __restrict__ rstar, const double* __restrict__ uhat,
                             double* __restrict__ T, double* __restrict__ F,
                             int* __restrict__ state, const int* __restrict__ status,
-                            int* __restrict__ iters) {
+                            int* __restrict__ iters, int* __restrict__ accurate) {
   const int c = blockIdx.y;
   const ChainDesc d = cd[c];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     state[c] = (status[c] == BD_OK) ? NS_ACTIVE : NS_FAILED;
     iters[c] = 0;
+    if (accurate) accurate[c] = 0;
   }
   if (i >= d.N) return;
   auto pred = [&](int b, double out[3]) {
@@ -140,9 +141,10 @@ __global__ void k_predictor(const double* __restrict__ r, const double* __restri
 
 cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* cd, int n_chains,
                              int max_N, Phys ph, double* rstar, const double* uhat, double* T, double* F,
-                             int* state, const int* status, int* iters, cudaStream_t s) {
+                             int* state, const int* status, int* iters, int* accurate, cudaStream_t s) {
   k_predictor<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, y, cd, n_chains, ph, rstar,
-                                                                    uhat, T, F, state, status, iters);
+                                                                    uhat, T, F, state, status, iters,
+                                                                    accurate);
   return cudaGetLastError();
 }
 
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
                                                          double* __restrict__ rhs,
                                                          int* __restrict__ state,
                                                          int* __restrict__ status,
-                                                         const int* __restrict__ iters) {
+                                                         const int* __restrict__ iters,
+                                                         int* __restrict__ accurate) {
   __shared__ double red[32];
   const int c = blockIdx.x;
   const int st = state[c];
@@ -180,22 +183,25 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
   gmax = block_max(gmax, red);
   if (threadIdx.x == 0) {
     int ns = st;
+    const bool acc_now = !accurate || accurate[c];
     if (st == NS_EXTRA) {
       ns = NS_DONE;
-    } else if (gmax <= ph.tol) {
+    } else if (gmax <= ph.tol && acc_now) {
       ns = NS_EXTRA;
     } else if (iters[c] >= ph.max_newton || !(gmax < INFINITY)) {
       ns = NS_FAILED;
       atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
     }
     state[c] = ns;
+    // the residual decides convergence only when it was evaluated accurately
+    if (accurate && gmax < 1e-5) accurate[c] = 1;
   }
 }
 
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs, int* state,
-                                   int* status, const int* iters, cudaStream_t s) {
-  k_newton_residual<<<n_chains, 256, 0, s>>>(rstar, u, cd, ph, rT, rhs, state, status, iters);
+                                   int* status, const int* iters, int* accurate, cudaStream_t s) {
+  k_newton_residual<<<n_chains, 256, 0, s>>>(rstar, u, cd, ph, rT, rhs, state, status, iters, accurate);
   return cudaGetLastError();
 }
 

@@ -19,47 +19,63 @@ constexpr int LDA = 129;  // 128 + 1
 constexpr int SB = 16;
 constexpr int kPotrfThreads = 512;
 
-// 16 x 16 leaf at offset o: L (into A) and W_oo (into W), one warp, lane r
-// holding row r; pivots and rows are broadcast with shuffles.
+// 16 x 16 leaf at offset o: L (into A) and W_oo (into W), one warp.  Lane r
+// holds row r of the block; at step j the column j just scaled is published
+// to shared memory (in place in A) and read back by every lane as broadcasts,
+// so the serial chain is one store, one warp barrier and independent loads
+// per pivot.  The inverse is formed column by column (lane = column) from L
+// in shared memory.
 __device__ __forceinline__ void leaf16(float* A, float* W, int o, int* bad) {
   const int lane = threadIdx.x & 31;
   if ((threadIdx.x >> 5) == 0) {
     const int r = lane & (SB - 1);
+    const bool own = lane < SB;
+    float* Ab = A + o * LDA + o;  // block origin
     float a[SB];
 #pragma unroll
-    for (int q = 0; q < SB; ++q) a[q] = (q <= r) ? A[(o + r) * LDA + o + q] : 0.0f;
+    for (int q = 0; q < SB; ++q) a[q] = (q <= r) ? Ab[r * LDA + q] : 0.0f;
     bool badl = false;
 #pragma unroll
     for (int j = 0; j < SB; ++j) {
-      const float djj = __shfl_sync(0xffffffffu, a[j], j);
+      // pivot: lane j's diagonal entry, read from shared memory after lane j
+      // wrote it in the previous step (step 0: the loaded value)
+      const float djj = (j == 0) ? Ab[0] : Ab[j * LDA + j];
       const bool ok = djj > 0.0f;
       badl |= !ok;
       const float inv = rsqrtf(ok ? djj : 1.0f);
       if (r == j) a[j] = (ok ? djj : 1.0f) * inv;
       else if (r > j) a[j] *= inv;
+      if (own && r >= j) Ab[r * LDA + j] = a[j];  // column j of L
+      __syncwarp();
+      float lq[SB];
 #pragma unroll
-      for (int q = j + 1; q < SB; ++q) {
-        const float lq = __shfl_sync(0xffffffffu, a[j], q);
-        if (r >= q) a[q] -= a[j] * lq;
+      for (int q = j + 1; q < SB; ++q) lq[q] = Ab[q * LDA + j];
+#pragma unroll
+      for (int q = j + 1; q < SB; ++q)
+        if (r >= q) a[q] -= a[j] * lq[q];
+      // next pivot entry becomes visible to everyone
+      if (j + 1 < SB && own && r == j + 1) Ab[r * LDA + j + 1] = a[j + 1];
+      __syncwarp();
+    }
+    if (own) {
+#pragma unroll
+      for (int q = 0; q < SB; ++q)
+        if (q <= r) Ab[r * LDA + q] = a[q];
+    }
+    __syncwarp();
+    if (own) {  // column `lane` of the inverse
+      float w[SB];
+#pragma unroll
+      for (int i = 0; i < SB; ++i) {
+        float sacc = (i == r) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int m = 0; m < i; ++m) sacc -= Ab[i * LDA + m] * w[m];
+        w[i] = (i >= r) ? sacc / Ab[i * LDA + i] : 0.0f;
       }
-    }
-    float w[SB];
 #pragma unroll
-    for (int i = 0; i < SB; ++i) {
-      float sacc = (i == r) ? 1.0f : 0.0f;
-#pragma unroll
-      for (int m = 0; m < i; ++m) sacc -= __shfl_sync(0xffffffffu, a[m], i) * w[m];
-      const float lii = __shfl_sync(0xffffffffu, a[i], i);
-      w[i] = (i >= r) ? sacc / lii : 0.0f;
+      for (int i = 0; i < SB; ++i) W[(o + i) * LDA + o + lane] = w[i];
     }
-    if (lane < SB) {
-#pragma unroll
-      for (int q = 0; q < SB; ++q) {
-        if (q <= r) A[(o + r) * LDA + o + q] = a[q];
-        W[(o + q) * LDA + o + lane] = w[q];
-      }
-    }
-    if (__any_sync(0xffffffffu, badl && lane < SB) && lane == 0) *bad = 1;
+    if (__any_sync(0xffffffffu, badl && own) && lane == 0) *bad = 1;
   }
   __syncthreads();
 }
