@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
             "fp64": fp64,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
             "cpu_baseline": cpu, "chain_status_ok": bool((st == 0).all()),
-            "max_rod_length_error": float(obs[:, bd.binding.OBS_STRIDE - 2].max().item()),
+            "max_rod_length_error": float(obs[:, bd.binding.OBS_MAXDEV].max().item()),
         }
         print(json.dumps(line))
 

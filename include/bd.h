@@ -64,14 +64,22 @@ typedef enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2 } bd_fl
 typedef enum { BD_FP64 = 0, BD_MIXED_TF32 = 1, BD_MIXED_BF16 = 2 } bd_precision;
 typedef enum { BD_RIGID = 0 } bd_constraint;
 
-/* Observables written per chain by bd_observables (Sec. 5 Eqs. (25)-(27)). */
-#define BD_OBS_STRIDE 8
+/* Observables written per chain by bd_observables (Sec. 5 Eqs. (25)-(29)). */
+#define BD_OBS_STRIDE 12
 #define BD_OBS_REE_X 0     /* r_{N-1} - r_0, three components */
 #define BD_OBS_R2 3        /* |R_ee|^2 */
 #define BD_OBS_RG2 4       /* radius of gyration squared */
 #define BD_OBS_STRETCH 5   /* |R_ee| / (N-1) */
 #define BD_OBS_MAXDEV 6    /* max_k | |Q_k| - 1 | */
 #define BD_OBS_NEWTON 7    /* Newton updates in the last step */
+/* Rod part of the Kramers stress, Eq. (28), with the rod force T_k Q_k (|Q_k|
+ * = 1, T_k the tension of the last step) in place of the spring force:
+ * sum_k T_k Q_k,a Q_k,b.  The isotropic N delta_ab and the ensemble average
+ * are the caller's; N1 = tau_xx - tau_yy (Eq. (29)). */
+#define BD_OBS_TAU_XX 8
+#define BD_OBS_TAU_YY 9
+#define BD_OBS_TAU_ZZ 10
+#define BD_OBS_TAU_XY 11
 
 typedef struct {
   int n_chains;          /* >= 1 */

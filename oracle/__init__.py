@@ -28,7 +28,7 @@ OK = 0
 ERR_NOT_PD = -4
 ERR_CONSTRAINT = -5
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
-OBS_STRIDE = 8
+OBS_STRIDE = 12
 
 
 class Params(ctypes.Structure):
@@ -86,7 +86,7 @@ def lib():
         L.or_step.restype = ctypes.c_int
         L.or_run.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ip, dp, ctypes.c_int,
                              dp, dp, ip, ip, dp]
-        L.or_observables.argtypes = [ctypes.c_int, dp, dp]
+        L.or_observables.argtypes = [ctypes.c_int, dp, dp, dp]
         L.or_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -203,8 +203,13 @@ def run(params: Params, Nc, r, noise):
     return r, T[: int(Nc.sum()) - nc], status, iters, maxdev
 
 
-def observables(r):
+def observables(r, T=None):
+    """Per-chain observables of Sec. 5 Eqs. (25)-(29); T: tensions of the rods."""
     r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
     out = np.zeros(OBS_STRIDE)
-    lib().or_observables(r.shape[0], _d(r), _d(out))
+    Tp = None
+    if T is not None:
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        Tp = _d(T)
+    lib().or_observables(r.shape[0], _d(r), Tp, _d(out))
     return out

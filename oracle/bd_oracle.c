@@ -364,8 +364,8 @@ void or_run(const or_params* p, int n_chains, const int* Nc, double* r,
   free(toff);
 }
 
-/* Sec. 5 Eqs. (25)-(27), per chain (the ensemble average is the caller's). */
-void or_observables(int N, const double* r, double* out) {
+/* Sec. 5 Eqs. (25)-(29), per chain (the ensemble average is the caller's). */
+void or_observables(int N, const double* r, const double* T, double* out) {
   double cm[3] = {0, 0, 0};
   for (int i = 0; i < N; ++i)
     for (int c = 0; c < 3; ++c) cm[c] += r[3 * i + c] / N;
@@ -396,4 +396,18 @@ void or_observables(int N, const double* r, double* out) {
   out[5] = N > 1 ? sqrt(R2) / (N - 1) : 0.0;
   out[6] = md;
   out[7] = 0.0;
+  /* Eq. (28): sum over rods of (force in rod k) (link vector k), tension part */
+  double txx = 0.0, tyy = 0.0, tzz = 0.0, txy = 0.0;
+  for (int k = 0; T && k + 1 < N; ++k) {
+    double q[3];
+    for (int c = 0; c < 3; ++c) q[c] = r[3 * (k + 1) + c] - r[3 * k + c];
+    txx += T[k] * q[0] * q[0];
+    tyy += T[k] * q[1] * q[1];
+    tzz += T[k] * q[2] * q[2];
+    txy += T[k] * q[0] * q[1];
+  }
+  out[8] = txx;
+  out[9] = tyy;
+  out[10] = tzz;
+  out[11] = txy;
 }

@@ -35,7 +35,7 @@ extern "C" {
 #define OR_FLOW_SHEAR 1
 #define OR_FLOW_UNIAXIAL 2
 
-#define OR_OBS_STRIDE 8 /* Rx Ry Rz R2 Rg2 stretch max||Q|-1| newton_iters */
+#define OR_OBS_STRIDE 12 /* Rx Ry Rz R2 Rg2 stretch max||Q|-1| newton_iters tau_xx tau_yy tau_zz tau_xy */
 
 typedef struct {
   double hstar;    /* HI parameter h* (>= 0) */
@@ -87,10 +87,13 @@ void or_run(const or_params* p, int n_chains, const int* Nc, double* r,
             int n_steps, const double* noise, double* T_out, int* status,
             int* iters, double* maxdev);
 
-/* Per-chain observables, Sec. 5 Eqs. (25)-(27):
+/* Per-chain observables, Sec. 5 Eqs. (25)-(29):
  * out[0..2] = r_{N-1} - r_0, out[3] = |R_ee|^2, out[4] = Rg^2,
- * out[5] = |R_ee| / (N-1), out[6] = max_k | |Q_k| - 1 |, out[7] = 0. */
-void or_observables(int N, const double* r, double* out);
+ * out[5] = |R_ee| / (N-1), out[6] = max_k | |Q_k| - 1 |, out[7] = 0,
+ * out[8..11] = sum_k T_k Q_k,a Q_k,b for ab = xx, yy, zz, xy: the rod part of
+ * the Kramers stress of Eq. (28) with the rod force T_k Q_k / |Q_k| (|Q_k| = 1)
+ * in place of the spring force; T may be NULL (zero tensions). */
+void or_observables(int N, const double* r, const double* T, double* out);
 
 int or_num_threads(void);
 

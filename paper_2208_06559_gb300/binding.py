@@ -27,7 +27,10 @@ BD_ERR_STATE = -7
 
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
-OBS_STRIDE = 8
+OBS_STRIDE = 12
+# column indices of the observables row (include/bd.h BD_OBS_*)
+OBS_REE_X, OBS_R2, OBS_RG2, OBS_STRETCH, OBS_MAXDEV, OBS_NEWTON = 0, 3, 4, 5, 6, 7
+OBS_TAU_XX, OBS_TAU_YY, OBS_TAU_ZZ, OBS_TAU_XY = 8, 9, 10, 11
 
 _lib = None
 

@@ -112,7 +112,7 @@ cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_b
                             const double* rT, double* r, const int* state, int* status,
                             StepArgs* args, cudaStream_t s);
 cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chains,
-                               const int* iters, double* obs, cudaStream_t s);
+                               const int* iters, const double* T, double* obs, cudaStream_t s);
 cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
                             cudaStream_t s);
 // FP32 Cholesky of the rod-coupling matrix with 64-wide tiles (k_chol_k64.cu);

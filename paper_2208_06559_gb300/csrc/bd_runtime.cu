@@ -686,7 +686,7 @@ int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_observables(c->r, c->d_cd, c->n_chains, c->iters, c->obs, s));
+  CK(launch_observables(c->r, c->d_cd, c->n_chains, c->iters, c->T, c->obs, s));
   if (obs)
     CK(cudaMemcpyAsync(obs, c->obs, (size_t)c->n_chains * BD_OBS_STRIDE * sizeof(double),
                        cudaMemcpyDefault, s));

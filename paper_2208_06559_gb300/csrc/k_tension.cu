@@ -397,6 +397,7 @@ cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_b
 __global__ void __launch_bounds__(256) k_observables(const double* __restrict__ r,
                                                      const ChainDesc* __restrict__ cd,
                                                      const int* __restrict__ iters,
+                                                     const double* __restrict__ T,
                                                      double* __restrict__ obs) {
   __shared__ double red[32];
   const int c = blockIdx.x;
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(256) k_observables(const double* __restrict__ 
   }
   const double cx = block_sum(s0, red) / d.N, cy = block_sum(s1, red) / d.N,
                cz = block_sum(s2, red) / d.N;
-  double g = 0.0, md = 0.0;
+  double g = 0.0, md = 0.0, txx = 0.0, tyy = 0.0, tzz = 0.0, txy = 0.0;
   for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
     const double dx = rc[3 * i] - cx, dy = rc[3 * i + 1] - cy, dz = rc[3 * i + 2] - cz;
     g += dx * dx + dy * dy + dz * dz;
@@ -418,10 +419,19 @@ __global__ void __launch_bounds__(256) k_observables(const double* __restrict__ 
       const double q0 = rc[3 * i + 3] - rc[3 * i], q1 = rc[3 * i + 4] - rc[3 * i + 1],
                    q2 = rc[3 * i + 5] - rc[3 * i + 2];
       md = fmax(md, fabs(sqrt(q0 * q0 + q1 * q1 + q2 * q2) - 1.0));
+      const double t = T[d.roff + i];  // Eq. (28) with the rod force T_k Q_k
+      txx += t * q0 * q0;
+      tyy += t * q1 * q1;
+      tzz += t * q2 * q2;
+      txy += t * q0 * q1;
     }
   }
   const double rg2 = block_sum(g, red) / d.N;
   md = block_max(md, red);
+  txx = block_sum(txx, red);
+  tyy = block_sum(tyy, red);
+  tzz = block_sum(tzz, red);
+  txy = block_sum(txy, red);
   if (threadIdx.x == 0) {
     const double* e = rc + 3 * (d.N - 1);
     const double rx = e[0] - rc[0], ry = e[1] - rc[1], rz = e[2] - rc[2];
@@ -435,12 +445,16 @@ __global__ void __launch_bounds__(256) k_observables(const double* __restrict__ 
     o[5] = sqrt(R2) / (d.N - 1);
     o[6] = md;
     o[7] = (double)iters[c];
+    o[BD_OBS_TAU_XX] = txx;
+    o[BD_OBS_TAU_YY] = tyy;
+    o[BD_OBS_TAU_ZZ] = tzz;
+    o[BD_OBS_TAU_XY] = txy;
   }
 }
 
 cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chains,
-                               const int* iters, double* obs, cudaStream_t s) {
-  k_observables<<<n_chains, 256, 0, s>>>(r, cd, iters, obs);
+                               const int* iters, const double* T, double* obs, cudaStream_t s) {
+  k_observables<<<n_chains, 256, 0, s>>>(r, cd, iters, T, obs);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,11 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--once", action="store_true")
+    ap.add_argument("--sweep", default="", help="comma-separated bead counts: time one step per N")
     a = ap.parse_args()
+    if a.sweep:
+        sweep(a)
+        return
 
     prec = bd.FP64 if a.precision == "fp64" else bd.MIXED_TF32
     Nc = np.full(a.chains, a.beads, np.int32)
@@ -96,6 +100,50 @@ def main():
     res["status_ok"] = bool((st == 0).all())
     print(json.dumps({"chains": a.chains, "beads": a.beads, "precision": a.precision,
                       **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in res.items()}}))
+
+
+def sweep(a):
+    """Step time against chain length (the paper's N-scaling study, Sec. 5):
+    one line per N with the step time, the factorisation time and a power-law
+    exponent fitted to the step times."""
+    import torch
+
+    import paper_2208_06559_gb300 as bd
+    from paper_2208_06559_gb300 import inputs
+
+    prec = bd.FP64 if a.precision == "fp64" else bd.MIXED_TF32
+    rows = []
+    for N in [int(x) for x in a.sweep.split(",")]:
+        Nc = np.full(a.chains, N, np.int32)
+        ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec)
+        ctx.set_state(torch.from_numpy(inputs.random_walk(Nc, a.seed)).cuda())
+        xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 1, int(Nc.sum()), a.seed + 1)).cuda()
+        ctx.step(xi[0:1])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(xi[1:])
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / a.reps
+        ctx.assemble()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        ctx.factor()
+        f1.record()
+        torch.cuda.synchronize()
+        st, _ = ctx.chain_status()
+        ctx.close()
+        rows.append({"N": N, "chains": a.chains, "step_ms": round(step_ms, 4),
+                     "factor_ms": round(f0.elapsed_time(f1), 4),
+                     "chain_steps_per_s": round(a.chains / (step_ms / 1e3), 1),
+                     "status_ok": bool((st == 0).all())})
+        print(json.dumps(rows[-1]), flush=True)
+    if len(rows) >= 2:
+        x = np.log([r["N"] for r in rows])
+        y = np.log([r["step_ms"] for r in rows])
+        print(json.dumps({"fit_step_time_exponent": float(np.polyfit(x, y, 1)[0]),
+                          "precision": a.precision}))
 
 
 if __name__ == "__main__":

@@ -135,12 +135,17 @@ def test_step_parity_single_chain_n16_100_steps(bd):
 
 
 def test_step_parity_batch_n100_uniaxial(bd):
-    """8 chains of 100 beads, uniaxial extension Wi = 10, 100 steps."""
+    """8 chains of 100 beads, uniaxial extension Wi = 10, 100 steps; the
+    observables (Eqs. (25)-(29)) against the oracle's on the oracle's state."""
     r0, rg, rr, st, str_, obs, Tg, Tr, nl = run_both(bd, [100] * 8, 100, 1236, flow=2, Wi=10.0)
     assert (st == 0).all() and (str_ == 0).all()
     assert rel(rg, rr) < 1e-10
     assert obs[:, 6].max() < 1e-10
     np.testing.assert_allclose(Tg, Tr, rtol=1e-6, atol=1e-6)
+    for c in range(8):
+        ref = orc.observables(rr[100 * c:100 * (c + 1)], Tr[99 * c:99 * (c + 1)])
+        np.testing.assert_allclose(obs[c, [0, 1, 2, 3, 4, 5]], ref[[0, 1, 2, 3, 4, 5]], rtol=1e-9)
+        np.testing.assert_allclose(obs[c, 8:12], ref[8:12], rtol=1e-5, atol=1e-5 * np.abs(ref[8:12]).max())
 
 
 def test_step_parity_uneven_shear(bd):

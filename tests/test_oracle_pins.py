@@ -427,3 +427,30 @@ def test_observables_closed_forms():
     np.testing.assert_allclose(o[4], (N * N - 1) / 12.0, rtol=1e-14)
     np.testing.assert_allclose(o[5], 1.0)
     assert o[6] < 1e-15
+
+
+def test_kramers_stress_closed_forms():
+    """Rod part of the Kramers stress (Sec. 5 Eq. (28)) with the rod force
+    T_k Q_k: a straight chain along x gives tau_xx = sum T and nothing else;
+    along (1, 1, 0)/sqrt(2) it gives tau_xx = tau_yy = tau_xy = sum T / 2."""
+    N = 5
+    T = np.array([1.0, 2.0, -0.5, 3.0])
+    r = np.zeros((N, 3))
+    r[:, 0] = np.arange(N)
+    o = orc.observables(r, T)
+    np.testing.assert_allclose(o[8:12], [T.sum(), 0, 0, 0], atol=1e-15)
+    d = np.array([1.0, 1.0, 0.0]) / np.sqrt(2)
+    r2 = np.arange(N)[:, None] * d[None, :]
+    o2 = orc.observables(r2, T)
+    np.testing.assert_allclose(o2[8:12], [T.sum() / 2, T.sum() / 2, 0, T.sum() / 2], atol=1e-14)
+    np.testing.assert_allclose(orc.observables(r)[8:12], 0.0)
+
+
+def test_dumbbell_stress_in_extension():
+    """Dumbbell along x after one noise-free step of uniaxial extension: the
+    stress is the closed-form tension, N1 = tau_xx - tau_yy = rate/(2(1 - mu_par))."""
+    rate, dt = 10.0, 1e-3
+    p = orc.make_params(hstar=0.25, a=0.25, dt=dt, flow=orc.FLOW_UNIAXIAL, Wi=rate)
+    r1, T, st, it, md = orc.step(p, np.array([[0.0, 0, 0], [1.0, 0, 0]]), np.zeros((2, 3)))
+    o = orc.observables(r1, T)
+    np.testing.assert_allclose(o[8] - o[9], rate / (2 * (1 - mu_far(1.0, 0.25, 0.25)[0])), rtol=1e-12)
