@@ -6,7 +6,7 @@
 // condition number grows like N^2, so its factor must be FP32-accurate (the
 // TF32 tensor-core path is not).  Per block column k:
 //   potrf64 : one CTA factors the 64 x 64 diagonal tile and forms its inverse
-//             (the recursive shared-memory routine of the 128-wide path);
+//             (the register-blocked routine of the 128-wide path);
 //   trsm64  : L_ik = A_ik W_kk^T, 64 x 64 per CTA, 4 x 4 outputs per thread;
 //   update64: A_ij -= L_ik L_jk^T for the trailing lower tiles.
 // The 64 x 64 diagonal-tile inverses are kept for the tension solve.
@@ -16,37 +16,19 @@
 namespace bd {
 
 constexpr int K64 = 64;
-constexpr int kPotrf64Smem = 3 * K64 * LDA * 4 + 64;
+using RegPotrf64 = RegPotrf<K64>;
 
-__global__ void __launch_bounds__(kPotrfThreads) k_potrf64(float* __restrict__ K, float* __restrict__ Kinv,
-                                                           const ChainDesc* __restrict__ cd, int k,
-                                                           int* __restrict__ status) {
-  extern __shared__ uint8_t smem_raw[];
-  float* A = reinterpret_cast<float*>(smem_raw);  // [64][129]
-  float* W = A + K64 * LDA;
-  float* Tm = W + K64 * LDA;
-  int* bad = reinterpret_cast<int*>(Tm + K64 * LDA);
+__global__ void __launch_bounds__(RegPotrf64::kThreads) k_potrf64(float* __restrict__ K, float* __restrict__ Kinv,
+                                                                 const ChainDesc* __restrict__ cd, int k,
+                                                                 int* __restrict__ status) {
+  __shared__ __align__(16) float sm[RegPotrf64::kSmemFloats];
   const int c = blockIdx.x;
   const ChainDesc d = cd[c];
   if (k * K64 >= d.mp) return;
   float* base = K + d.koff + (long long)(k * K64) * d.mp + k * K64;
-  const long long mp = d.mp;
-  const int tid = threadIdx.x;
-  if (tid == 0) *bad = 0;
-  for (int e = tid; e < K64 * K64; e += kPotrfThreads) {
-    const int r = e >> 6, cc = e & 63;
-    A[r * LDA + cc] = (cc <= r) ? base[r * mp + cc] : 0.0f;
-    W[r * LDA + cc] = 0.0f;
-  }
-  __syncthreads();
-  potrf_rec<K64>(A, W, Tm, 0, bad);
   float* wout = Kinv + (d.kwrow + (long long)k * K64) * K64;
-  for (int e = tid; e < K64 * K64; e += kPotrfThreads) {
-    const int r = e >> 6, cc = e & 63;
-    if (cc <= r) base[r * mp + cc] = A[r * LDA + cc];
-    wout[e] = W[r * LDA + cc];
-  }
-  if (tid == 0 && *bad) atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
+  potrf_regs<K64>(base, d.mp, base, d.mp, wout, K64, sm);
+  if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf64::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
 }
 
 // 64 x 64 output tile, 256 threads, 4 x 4 outputs each.
@@ -118,14 +100,12 @@ __global__ void __launch_bounds__(256) k_gemm64(float* __restrict__ K, const flo
     }
 }
 
-cudaError_t k64_configure() {
-  return cudaFuncSetAttribute(k_potrf64, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrf64Smem);
-}
+cudaError_t k64_configure() { return cudaSuccess; }
 
 cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
                             int* status, cudaStream_t s) {
   for (int k = 0; k < max_tiles; ++k) {
-    k_potrf64<<<n_chains, kPotrfThreads, kPotrf64Smem, s>>>(K, Kinv, cd, k, status);
+    k_potrf64<<<n_chains, RegPotrf64::kThreads, 0, s>>>(K, Kinv, cd, k, status);
     const int below = max_tiles - 1 - k;
     if (below > 0) {
       k_gemm64<true><<<dim3(below, n_chains), 256, 0, s>>>(K, Kinv, cd, k);

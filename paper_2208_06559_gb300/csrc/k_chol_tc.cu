@@ -129,26 +129,56 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
       else
         tma_load_2d(sb, bm, &full[s], kx, tj * NB);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
+  } else if (warp == 1) {
+    // ---- MMA issuer (lane 0).  TRSM: the whole warp first meets the two
+    // rounding warps on the stage's named barrier.
     constexpr uint32_t idesc = idesc_mma(2u /*tf32*/, 128u, 128u);
     bool ok = true;
     for (int q = 0; q < nchunks; ++q) {
       const int s = q % kStages, round = q / kStages;
-      if (!mbar_wait(&full[s], round & 1)) {
+      if (MODE == TC_TRSM) {
+        if (s == 0) named_bar_sync<1, 96>();
+        else named_bar_sync<2, 96>();
+        if (*(volatile int*)fail) ok = false;
+      } else if (lane == 0 && ok && !mbar_wait(&full[s], round & 1)) {
         atomicExch(fail, 1);
         ok = false;
-        break;
       }
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * kStageBytes);
-      const uint64_t ad = desc_sw128(sa), bdsc = desc_sw128(sa + kChunkBytes);
+      if (MODE == TC_UPDATE && !__shfl_sync(0xffffffffu, ok, 0)) break;
+      if (lane == 0 && ok) {
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * kStageBytes);
+        const uint64_t ad = desc_sw128(sa), bdsc = desc_sw128(sa + kChunkBytes);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)  // K = 8 tf32 per MMA = 32 bytes of the 128-byte row
-        mma_tf32(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int kk = 0; kk < 4; ++kk)  // K = 8 tf32 per MMA = 32 bytes of the 128-byte row
+          mma_tf32(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      __syncwarp();
     }
-    if (ok) mma_commit(done);
+    if (lane == 0 && ok) mma_commit(done);
+  } else if (MODE == TC_TRSM && warp >= 2) {
+    // ---- warps 2-3 round both operand slices of each stage to TF32 in
+    // place (elementwise, so the swizzled layout does not matter) and hand
+    // the stage to the issuer; they always arrive, so the issuer never waits
+    // on them unboundedly.
+    const int t = threadIdx.x - 64;
+    for (int q = 0; q < nchunks; ++q) {
+      const int s = q % kStages, round = q / kStages;
+      if (!*(volatile int*)fail && !mbar_wait(&full[s], round & 1)) atomicExch(fail, 1);
+      if (!*(volatile int*)fail) {
+        float4* st = reinterpret_cast<float4*>(smem + s * kStageBytes);
+#pragma unroll 8
+        for (int e = t; e < kStageBytes / 16; e += 64) {
+          float4 v = st[e];
+          v.x = tf32_rna(v.x); v.y = tf32_rna(v.y); v.z = tf32_rna(v.z); v.w = tf32_rna(v.w);
+          st[e] = v;
+        }
+        fence_proxy_async_smem();
+      }
+      if (s == 0) named_bar_arrive<1, 96>();
+      else named_bar_arrive<2, 96>();
+    }
   }
   __syncwarp();
 
@@ -177,6 +207,8 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
           if (MODE == TC_UPDATE) {
             val = -val;
             if (diag && col > row) val = 0.0f;
+          } else {
+            val = tf32_rna(val);  // L tiles enter later products exactly
           }
           fp[e] = val;
         }
@@ -212,51 +244,28 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
 }
 
 // ------------------------------------------------------------ potrf128
-// One CTA (512 threads) per chain factors the 128 x 128 diagonal tile k in
-// place and writes W = L_kk^{-1} (lower, zeros above) to rows
-// wrow + 128 k .. of Winv (kept for the refinement's triangular solve).
-// Recursive halving 128 -> 64 -> 32 -> 16: for a block [[A11, .], [A21, A22]]
-//   factor A11 -> L11, W11;  L21 = A21 W11^T;  A22 -= L21 L21^T;
-//   factor A22 -> L22, W22;  W21 = -W22 (L21 W11);
-// every product is split evenly over the 512 threads with register blocking;
-// the 16 x 16 leaves are factored by one warp in registers (lane r holds row
-// r, pivots broadcast by shuffles) together with their inverses.  All in
+// One CTA (544 threads, 528 owning a 4 x 4 block of the lower triangle) per
+// chain factors the 128 x 128 diagonal tile k in place and writes
+// W = L_kk^{-1} (lower, zeros above) to rows wrow + 128 k .. of Winv (kept for
+// the refinement's triangular solve), by the register-blocked right-looking
+// elimination of [A | I] in potrf_dev.h: 128 steps, one barrier each.  All in
 // FP32: on this part FP64 issues at 1/64 of the FP32 rate, and the FP32
 // rounding of this tile (~1e-7 relative) is far below the TF32 rounding of
 // the products around it.
-constexpr int kPotrfSmem = 3 * NB * LDA * 4 + 64;
+using RegPotrf128 = RegPotrf<NB>;
 
-__global__ void __launch_bounds__(kPotrfThreads) k_potrf128(float* __restrict__ M,
-                                                            float* __restrict__ Winv,
-                                                            const ChainDesc* __restrict__ cd, int k,
-                                                            int* __restrict__ status) {
-  extern __shared__ uint8_t smem_raw[];
-  float* A = reinterpret_cast<float*>(smem_raw);  // [128][129] tile, then L
-  float* W = A + NB * LDA;                         // [128][129] inverse
-  float* Tm = W + NB * LDA;                        // [128][129] scratch
-  int* bad = reinterpret_cast<int*>(Tm + NB * LDA);
+__global__ void __launch_bounds__(RegPotrf128::kThreads) k_potrf128(float* __restrict__ M,
+                                                                   float* __restrict__ Winv,
+                                                                   const ChainDesc* __restrict__ cd, int k,
+                                                                   int* __restrict__ status) {
+  __shared__ __align__(16) float sm[RegPotrf128::kSmemFloats];
   const int c = blockIdx.x;
   const ChainDesc d = cd[c];
   if (k * NB >= d.np) return;
   float* base = M + d.moff + (long long)(k * NB) * d.np + k * NB;
-  const long long np = d.np;
-  const int tid = threadIdx.x;
-  if (tid == 0) *bad = 0;
-  for (int e = tid; e < NB * NB; e += kPotrfThreads) {
-    const int r = e >> 7, cc = e & 127;
-    A[r * LDA + cc] = (cc <= r) ? base[r * np + cc] : 0.0f;
-    W[r * LDA + cc] = 0.0f;
-  }
-  __syncthreads();
-  potrf_rec<NB>(A, W, Tm, 0, bad);
-  // write back L_kk (lower) and W (full tile, zeros above the diagonal)
   float* wout = Winv + ((long long)d.wrow + (long long)k * NB) * NB;
-  for (int e = tid; e < NB * NB; e += kPotrfThreads) {
-    const int r = e >> 7, cc = e & 127;
-    if (cc <= r) base[r * np + cc] = A[r * LDA + cc];
-    wout[e] = W[r * LDA + cc];
-  }
-  if (tid == 0 && *bad) atomicCAS(status + c, BD_OK, BD_ERR_NOT_PD);
+  potrf_regs<NB>(base, d.np, base, d.np, wout, NB, sm);
+  if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf128::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_NOT_PD);
 }
 
 // ------------------------------------------------------------ host side
@@ -301,8 +310,6 @@ cudaError_t tc_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<TC_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_gemm<TC_TRSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_potrf128, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem);
   return e;
 }
 
@@ -328,7 +335,7 @@ cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const
       if (k > K0)
         k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, k, k + 1), n_chains), 128, kTcSmem, s>>>(
             maps, nullptr, cd, K0, k, k, k + 1, status);
-      k_potrf128<<<n_chains, kPotrfThreads, kPotrfSmem, s>>>(M, Winv, cd, k, status);
+      k_potrf128<<<n_chains, RegPotrf128::kThreads, 0, s>>>(M, Winv, cd, k, status);
       const int below = T - 1 - k;
       if (below > 0)
         k_tc_gemm<TC_TRSM><<<dim3(below, n_chains), 128, kTcSmem, s>>>(maps, wmap, cd, k, k + 1, 0, 0,

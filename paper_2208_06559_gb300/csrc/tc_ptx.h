@@ -84,6 +84,26 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // -------------------------------------------------------------- tcgen05
+// Round an FP32 value to TF32 (10-bit mantissa), to nearest with ties away
+// from zero; the tensor core ignores the low 13 mantissa bits of an FP32
+// operand (truncation), so operands rounded here enter the product exactly.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Named CTA barriers (ID 1..15; 0 is __syncthreads), N threads, a multiple
+// of 32.  Compile-time IDs so that only the barriers used are reserved.
+template <int ID, int N>
+__device__ __forceinline__ void named_bar_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int ID, int N>
+__device__ __forceinline__ void named_bar_arrive() {
+  asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                "r"(ncols)
