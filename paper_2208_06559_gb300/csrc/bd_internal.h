@@ -67,9 +67,15 @@ inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b
 template <typename T>
 cudaError_t launch_fill_identity_border(T* M, const ChainDesc* cd, int n_chains,
                                         int max_np, bool k_matrix, cudaStream_t s);
+// rsplit: [sum np] float2 scratch for the FP32 path's (hi, lo) positions
+// (unused by the FP64 path).
 template <typename T>
 cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_chains,
-                            int max_N, double hstar, double a, cudaStream_t s);
+                            int max_N, int max_np, double hstar, double a, float2* rsplit,
+                            cudaStream_t s);
+// v (FP64, per chain 3N values at 3 boff) -> (hi, lo) float pairs at swrow, zero-padded to np.
+cudaError_t launch_split_f2(const ChainDesc* cd, int n_chains, int max_np, const double* v,
+                            float2* out, const int* state, cudaStream_t s);
 template <typename T>
 cudaError_t launch_chol_simt(T* M, T* Winv, const ChainDesc* cd, int n_chains, int max_tiles,
                              bool k_matrix, int* status, cudaStream_t s);
@@ -81,10 +87,11 @@ template <typename T>
 cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_np,
                         const double* f, double* scratch, double* u, const int* state,
                         cudaStream_t s);
-// FP32-storage mobility product with a per-chain accuracy switch (see k_matvec.cu).
+// FP32-storage mobility product with a per-chain accuracy switch (see
+// k_matvec.cu).  fsplit: [sum np] float2, scratch: the two-phase partials.
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, double* scratch, double* u, const int* state,
-                            const int* accurate, cudaStream_t s);
+                            const double* f, float2* fsplit, double* scratch, double* u,
+                            const int* state, const int* accurate, cudaStream_t s);
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s);
@@ -125,6 +132,7 @@ cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_ch
 cudaError_t matvec_configure();
 cudaError_t assemble_configure();
 cudaError_t tension_configure();
+cudaError_t refine_configure();
 
 // Mixed-precision Brownian displacement with one refinement step (k_refine.cu):
 // y = s/2 (B xi + D B^{-T} xi); with refine == 0, y = s B xi.
@@ -133,7 +141,8 @@ cudaError_t tension_configure();
 cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
-                                double* scratch, cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev);
+                                double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
+                                cudaEvent_t* ev);
 
 // Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
 bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains);

@@ -43,6 +43,7 @@ struct bd_ctx {
   double *r = nullptr, *rstar = nullptr, *rT = nullptr, *y = nullptr, *u = nullptr, *F = nullptr;
   double *uhat = nullptr, *T = nullptr, *rhs = nullptr, *scratch = nullptr, *obs = nullptr;
   float* Winv = nullptr;           // mixed: inverses of the diagonal tiles, [sum np][128]
+  float2* fsplit = nullptr;        // mixed: (hi, lo) split of a mobility product's input, [sum np]
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
   CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
@@ -130,9 +131,11 @@ int enqueue_factor(bd_ctx* c, cudaStream_t s) {
 int enqueue_assemble(bd_ctx* c, cudaStream_t s) {
   const double a = c->ph.a;
   if (c->mixed)
-    CK(launch_assemble<float>(c->r, (float*)c->M, c->d_cd, c->n_chains, c->max_N, c->ph.hstar, a, s));
+    CK(launch_assemble<float>(c->r, (float*)c->M, c->d_cd, c->n_chains, c->max_N, c->max_np, c->ph.hstar,
+                              a, c->fsplit, s));
   else
-    CK(launch_assemble<double>(c->r, (double*)c->M, c->d_cd, c->n_chains, c->max_N, c->ph.hstar, a, s));
+    CK(launch_assemble<double>(c->r, (double*)c->M, c->d_cd, c->n_chains, c->max_N, c->max_np,
+                               c->ph.hstar, a, nullptr, s));
   return BD_OK;
 }
 
@@ -143,8 +146,8 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
   const double sc = c->ph.sq2dt;
   if (c->mixed)  // buffers rT, F, u are free at this point of the step
     CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, x, args, sc,
-                           c->p.refine != 0, y, c->rT, c->F, c->u, c->scratch, s, c->aux[1],
-                           c->aev + 2));
+                           c->p.refine != 0, y, c->rT, c->F, c->u, c->scratch, c->fsplit, s,
+                           c->aux[1], c->aev + 2));
   else
     CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, x, args, sc, y, s));
   return BD_OK;
@@ -152,8 +155,8 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
 
 int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv<float>((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
-                          state, s));
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->fsplit, c->scratch,
+                       u, state, nullptr, s));
   else
     CK(launch_symv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
                            state, s));
@@ -194,8 +197,8 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
 // sums while a chain's residual is large, compensated (FP64-level) after.
 int enqueue_newton_symv(bd_ctx* c, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->scratch, c->u,
-                       c->state, c->accurate, s));
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->fsplit,
+                       c->scratch, c->u, c->state, c->accurate, s));
   else
     return enqueue_symv(c, c->F, c->u, c->state, s);
   return BD_OK;
@@ -424,7 +427,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -558,6 +561,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
        (c->mixed || alloc(&c->Minv, (size_t)swrow * kSimtTile * c->elem));
   if (ok && c->mixed)
     ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
+         alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) &&
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
@@ -593,7 +597,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       return fail(BD_ERR_CUDA);
   }
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
-      assemble_configure() != cudaSuccess ||
+      assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
       k64_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,

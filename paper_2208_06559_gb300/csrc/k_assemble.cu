@@ -40,10 +40,14 @@ __device__ __forceinline__ void rpy_coeffs(C R2, C hstar, C a, C& cI, C& cRR) {
   }
 }
 
+// FP32 path: the positions arrive split into (hi, lo) float pairs (rs), and
+// every difference is (x_i,hi - x_j,hi) + (x_i,lo - x_j,lo): exact for nearby
+// beads (Sterbenz), FP32-accurate otherwise, with no FP64 arithmetic (the
+// FP64 pipe of this part runs at 1/64 of the FP32 rate).
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, T* __restrict__ M,
-                                                  const ChainDesc* __restrict__ cd, double hstar,
-                                                  double a) {
+__global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, const float2* __restrict__ rs,
+                                                  T* __restrict__ M, const ChainDesc* __restrict__ cd,
+                                                  double hstar, double a) {
   using C = T;  // arithmetic type of the coefficients (FP64 or FP32)
   extern __shared__ __align__(16) uint8_t as_smem[];
   T (*S)[kElTile + 1] = reinterpret_cast<T (*)[kElTile + 1]>(as_smem);
@@ -51,7 +55,7 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
   const int TB = (d.N + kBeadTile - 1) / kBeadTile;
   const int p = blockIdx.x;
   if (p >= TB * (TB + 1) / 2) return;
-  int bi = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  int bi = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
   while (bi * (bi + 1) / 2 > p) --bi;
   while ((bi + 1) * (bi + 2) / 2 <= p) ++bi;
   const int bj = p - bi * (bi + 1) / 2;  // bj <= bi
@@ -68,11 +72,22 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
       if (i == j) {
         blk[0] = blk[4] = blk[8] = T(1);
       } else {
-        const double* ri = r + 3 * (d.boff + i);
-        const double* rj = r + 3 * (d.boff + j);
-        const double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
-        const C R[3] = {(C)dx, (C)dy, (C)dz};
-        const C R2 = (C)(dx * dx + dy * dy + dz * dz);
+        C R[3], R2;
+        if constexpr (sizeof(T) == 4) {
+          const float2* ri = rs + d.swrow + 3 * i;
+          const float2* rj = rs + d.swrow + 3 * j;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) R[k] = (ri[k].x - rj[k].x) + (ri[k].y - rj[k].y);
+          R2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+        } else {
+          const double* ri = r + 3 * (d.boff + i);
+          const double* rj = r + 3 * (d.boff + j);
+          const double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
+          R[0] = dx;
+          R[1] = dy;
+          R[2] = dz;
+          R2 = dx * dx + dy * dy + dz * dz;
+        }
         C cI, cRR;
         rpy_coeffs<C>(R2, (C)hstar, (C)a, cI, cRR);
 #pragma unroll
@@ -107,10 +122,15 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
 
 template <typename T>
 cudaError_t launch_assemble(const double* r, T* M, const ChainDesc* cd, int n_chains, int max_N,
-                            double hstar, double a, cudaStream_t s) {
+                            int max_np, double hstar, double a, float2* rsplit, cudaStream_t s) {
+  if (sizeof(T) == 4) {
+    if (!rsplit) return cudaErrorInvalidValue;
+    const cudaError_t e = launch_split_f2(cd, n_chains, max_np, r, rsplit, nullptr, s);
+    if (e != cudaSuccess) return e;
+  }
   const int TB = (max_N + kBeadTile - 1) / kBeadTile;
   dim3 grid(TB * (TB + 1) / 2, n_chains);
-  k_assemble<T><<<grid, 256, assemble_smem<T>(), s>>>(r, M, cd, hstar, a);
+  k_assemble<T><<<grid, 256, assemble_smem<T>(), s>>>(r, rsplit, M, cd, hstar, a);
   return cudaGetLastError();
 }
 
@@ -159,10 +179,10 @@ cudaError_t launch_extract(const T* M, const ChainDesc* cd, int chain, int which
   return cudaGetLastError();
 }
 
-template cudaError_t launch_assemble<double>(const double*, double*, const ChainDesc*, int, int,
-                                             double, double, cudaStream_t);
-template cudaError_t launch_assemble<float>(const double*, float*, const ChainDesc*, int, int,
-                                            double, double, cudaStream_t);
+template cudaError_t launch_assemble<double>(const double*, double*, const ChainDesc*, int, int, int,
+                                             double, double, float2*, cudaStream_t);
+template cudaError_t launch_assemble<float>(const double*, float*, const ChainDesc*, int, int, int,
+                                            double, double, float2*, cudaStream_t);
 template cudaError_t launch_fill_identity_border<double>(double*, const ChainDesc*, int, int, bool,
                                                          cudaStream_t);
 template cudaError_t launch_fill_identity_border<float>(float*, const ChainDesc*, int, int, bool,

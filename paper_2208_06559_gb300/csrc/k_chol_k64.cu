@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_gemm64(float* __restrict__ K, const flo
     const int s = T - k - 1;
     const int p = blockIdx.x;
     if (s <= 0 || p >= s * (s + 1) / 2) return;
-    int ii = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+    int ii = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
     while (ii * (ii + 1) / 2 > p) --ii;
     while ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
     i = k + 1 + ii;

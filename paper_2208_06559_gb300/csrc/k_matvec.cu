@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
   const int TK = (m + KR - 1) / KR;
   const int p = blockIdx.x;
   if (p >= TK * (TK + 1) / 2) return;
-  int kt = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  int kt = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
   while (kt * (kt + 1) / 2 > p) --kt;
   while ((kt + 1) * (kt + 2) / 2 <= p) ++kt;
   const int lt = p - kt * (kt + 1) / 2;  // lt <= kt
@@ -269,16 +269,23 @@ template cudaError_t launch_form_k<float>(const float*, float*, const ChainDesc*
 namespace bd {
 
 // ---------------------------------------------------- symv, FP32 storage
-// u = D f for D stored in FP32, to FP64-level accuracy without FP64 products:
-// each f value is split into two floats (f = fh + fl), every product d*fh is
-// made exact with an FMA (p + e), the p terms are summed with a compensated
-// (two-sum) accumulator and the small terms in a plain float.  A 64 x 64 tile
-// is staged in shared memory (128 threads: thread t < 64 sums row t, thread
-// t >= 64 column t - 64), so each element is read from HBM once and used
-// twice; small CTAs let about a dozen share an SM, overlapping one tile's
-// loads with another's sums.  Diagonal tiles are symmetrised in shared memory
-// (mirror of the upper part, unit diagonal) and only row sums are taken.
-// Partial sums go to the same two-phase scratch as the FP64 version.
+// u = D f for D stored in FP32, to FP64-level accuracy with FP32 arithmetic
+// only (the FP64 pipe of this part runs at 1/64 of the FP32 rate):
+//   k_split_f2      : f (FP64) -> (fh, fl) float pairs once per product,
+//                     zero-padded to the chain's padded order;
+//   k_symv_tiles_f32: per 64 x 64 tile of the upper triangle, every product
+//                     d*fh is made exact with an FMA (p + e), the p terms are
+//                     summed with a compensated (two-sum) accumulator and the
+//                     small terms in a plain float; row sums and column sums
+//                     of the tile go out as (hi, lo) pairs;
+//   k_symv_reduce_df: per row, compensated sum of its tile partials, one
+//                     conversion to FP64.
+// A tile is staged in shared memory (128 threads: thread t < 64 sums row t,
+// thread t >= 64 column t - 64), so each element is read from HBM once and
+// used twice; small CTAs let about a dozen share an SM, overlapping one
+// tile's loads with another's sums.  Diagonal tiles are symmetrised in
+// shared memory (mirror of the upper part, unit diagonal) and only row sums
+// are taken.
 constexpr int SF = 64;
 constexpr int SFP = SF + 4;  // row pitch: 16-byte aligned rows for float4 access
 
@@ -296,29 +303,47 @@ __device__ __forceinline__ void df_add_prod(DF& a, float d, float fh, float fl) 
   a.lo += err + e + d * fl;
 }
 
-constexpr int kSymvF32Smem = (SF * SFP + 4 * SF) * 4;
+// (bj, bi), bi <= bj, of upper-triangle tile p (column-major enumeration),
+// in FP32 with an exact integer correction.
+__device__ __forceinline__ void upper_tile_of(int p, int& bi, int& bj) {
+  int j = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while (j * (j + 1) / 2 > p) --j;
+  while ((j + 1) * (j + 2) / 2 <= p) ++j;
+  bj = j;
+  bi = p - j * (j + 1) / 2;
+}
+
+__global__ void k_split_f2(const ChainDesc* __restrict__ cd, const double* __restrict__ f,
+                           float2* __restrict__ fs, const int* __restrict__ state) {
+  const int c = blockIdx.y;
+  if (state && state[c] >= NS_DONE) return;
+  const ChainDesc d = cd[c];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.np) return;
+  const double v = (e < d.n) ? f[3 * d.boff + e] : 0.0;
+  const float h = (float)v;
+  fs[d.swrow + e] = make_float2(h, (float)(v - (double)h));
+}
 
 // `accurate` (per chain, may be NULL = always): 0 selects plain FP32 sums
 // (relative error ~1e-7), used by the tension iteration while its residual
 // is still large.
 __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict__ M,
                                                         const ChainDesc* __restrict__ cd,
-                                                        const double* __restrict__ f,
-                                                        double* __restrict__ P,
+                                                        const float2* __restrict__ fs,
+                                                        float2* __restrict__ P,
                                                         const int* __restrict__ state,
                                                         const int* __restrict__ accurate) {
   __shared__ __align__(16) float S[SF][SFP];
-  __shared__ float frh[SF], frl[SF], fch[SF], fcl[SF];
+  __shared__ __align__(16) float frh[SF], frl[SF], fch[SF], fcl[SF];
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
   const int TSn = (d.n + SF - 1) / SF;
   const int p = blockIdx.x;
   if (p >= TSn * (TSn + 1) / 2) return;
-  int bj = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
-  while (bj * (bj + 1) / 2 > p) --bj;
-  while ((bj + 1) * (bj + 2) / 2 <= p) ++bj;
-  const int bi = p - bj * (bj + 1) / 2;  // bi <= bj
+  int bi, bj;
+  upper_tile_of(p, bi, bj);
   const bool diag = (bi == bj);
   const int r0 = bi * SF, c0 = bj * SF;
   const float* base = M + d.moff + (long long)r0 * d.np + c0;
@@ -333,13 +358,11 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
         __ldg(reinterpret_cast<const float4*>(base + (long long)r * np + 4 * c4));
   }
   if (t < SF) {
-    const double* fb = f + 3 * d.boff;
-    const double a = (r0 + t < d.n) ? fb[r0 + t] : 0.0;
-    const double b = (c0 + t < d.n) ? fb[c0 + t] : 0.0;
-    frh[t] = (float)a;
-    frl[t] = (float)(a - (double)frh[t]);
-    fch[t] = (float)b;
-    fcl[t] = (float)(b - (double)fch[t]);
+    const float2 a = fs[d.swrow + r0 + t], b = fs[d.swrow + c0 + t];
+    frh[t] = a.x;
+    frl[t] = a.y;
+    fch[t] = b.x;
+    fcl[t] = b.y;
   }
   __syncthreads();
   if (diag) {
@@ -352,25 +375,32 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
     __syncthreads();
   }
   const long long ld = (long long)TSn * SF;
-  double* Pc = P + d.soff;
+  float2* Pc = P + d.soff;
   if (accurate && accurate[c] == 0) {
     if (t < SF) {
       float acc = 0.f;
 #pragma unroll 4
       for (int q4 = 0; q4 < SF / 4; ++q4) {
         const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
-        acc = fmaf(v.x, fch[4 * q4], acc);
-        acc = fmaf(v.y, fch[4 * q4 + 1], acc);
-        acc = fmaf(v.z, fch[4 * q4 + 2], acc);
-        acc = fmaf(v.w, fch[4 * q4 + 3], acc);
+        const float4 fh = *reinterpret_cast<const float4*>(&fch[4 * q4]);
+        acc = fmaf(v.x, fh.x, acc);
+        acc = fmaf(v.y, fh.y, acc);
+        acc = fmaf(v.z, fh.z, acc);
+        acc = fmaf(v.w, fh.w, acc);
       }
-      Pc[bj * ld + r0 + t] = (double)acc;
+      Pc[bj * ld + r0 + t] = make_float2(acc, 0.f);
     } else if (!diag) {
       const int q = t - SF;
       float acc = 0.f;
-#pragma unroll 8
-      for (int r = 0; r < SF; ++r) acc = fmaf(S[r][q], frh[r], acc);
-      Pc[bi * ld + c0 + q] = (double)acc;
+#pragma unroll 4
+      for (int r = 0; r < SF; r += 4) {
+        const float4 fh = *reinterpret_cast<const float4*>(&frh[r]);
+        acc = fmaf(S[r][q], fh.x, acc);
+        acc = fmaf(S[r + 1][q], fh.y, acc);
+        acc = fmaf(S[r + 2][q], fh.z, acc);
+        acc = fmaf(S[r + 3][q], fh.w, acc);
+      }
+      Pc[bi * ld + c0 + q] = make_float2(acc, 0.f);
     }
     return;
   }
@@ -379,54 +409,66 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
 #pragma unroll 4
     for (int q4 = 0; q4 < SF / 4; ++q4) {
       const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
-      df_add_prod(acc, v.x, fch[4 * q4], fcl[4 * q4]);
-      df_add_prod(acc, v.y, fch[4 * q4 + 1], fcl[4 * q4 + 1]);
-      df_add_prod(acc, v.z, fch[4 * q4 + 2], fcl[4 * q4 + 2]);
-      df_add_prod(acc, v.w, fch[4 * q4 + 3], fcl[4 * q4 + 3]);
+      const float4 fh = *reinterpret_cast<const float4*>(&fch[4 * q4]);
+      const float4 fl = *reinterpret_cast<const float4*>(&fcl[4 * q4]);
+      df_add_prod(acc, v.x, fh.x, fl.x);
+      df_add_prod(acc, v.y, fh.y, fl.y);
+      df_add_prod(acc, v.z, fh.z, fl.z);
+      df_add_prod(acc, v.w, fh.w, fl.w);
     }
-    Pc[bj * ld + r0 + t] = (double)acc.hi + (double)acc.lo;  // rows of bi from column block bj
+    Pc[bj * ld + r0 + t] = make_float2(acc.hi, acc.lo);  // rows of bi from column block bj
   } else if (!diag) {
     const int q = t - SF;
     DF acc{0.f, 0.f};
-#pragma unroll 8
-    for (int r = 0; r < SF; ++r) df_add_prod(acc, S[r][q], frh[r], frl[r]);
-    Pc[bi * ld + c0 + q] = (double)acc.hi + (double)acc.lo;  // rows of bj from column block bi
+#pragma unroll 4
+    for (int r = 0; r < SF; r += 4) {
+      const float4 fh = *reinterpret_cast<const float4*>(&frh[r]);
+      const float4 fl = *reinterpret_cast<const float4*>(&frl[r]);
+      df_add_prod(acc, S[r][q], fh.x, fl.x);
+      df_add_prod(acc, S[r + 1][q], fh.y, fl.y);
+      df_add_prod(acc, S[r + 2][q], fh.z, fl.z);
+      df_add_prod(acc, S[r + 3][q], fh.w, fl.w);
+    }
+    Pc[bi * ld + c0 + q] = make_float2(acc.hi, acc.lo);  // rows of bj from column block bi
   }
 }
 
-__global__ void k_symv_reduce_w(const ChainDesc* __restrict__ cd, const double* __restrict__ P,
-                                double* __restrict__ u, const int* __restrict__ state, int width) {
+__global__ void k_symv_reduce_df(const ChainDesc* __restrict__ cd, const float2* __restrict__ P,
+                                 double* __restrict__ u, const int* __restrict__ state) {
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= d.n) return;
-  const int TSn = (d.n + width - 1) / width;
-  const long long ld = (long long)TSn * width;
-  const double* Pc = P + d.soff;
-  double s = 0.0;
-  for (int t = 0; t < TSn; ++t) s += Pc[t * ld + row];
-  u[3 * d.boff + row] = s;
+  const int TSn = (d.n + SF - 1) / SF;
+  const long long ld = (long long)TSn * SF;
+  const float2* Pc = P + d.soff;
+  float hi = 0.f, lo = 0.f;
+  for (int t = 0; t < TSn; ++t) {
+    const float2 v = Pc[t * ld + row];
+    const float s = hi + v.x;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (v.x - bp)) + v.y;
+    hi = s;
+  }
+  u[3 * d.boff + row] = (double)hi + (double)lo;
 }
 
-cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, double* scratch, double* u, const int* state,
-                            const int* accurate, cudaStream_t s) {
-  const int TSn = ceil_div(max_np, SF);
-  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state,
-                                                                        accurate);
-  k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
+cudaError_t launch_split_f2(const ChainDesc* cd, int n_chains, int max_np, const double* v,
+                            float2* out, const int* state, cudaStream_t s) {
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, v, out, state);
   return cudaGetLastError();
 }
 
-template <>
-cudaError_t launch_symv<float>(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                               const double* f, double* scratch, double* u, const int* state,
-                               cudaStream_t s) {
+cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
+                            const double* f, float2* fsplit, double* scratch, double* u,
+                            const int* state, const int* accurate, cudaStream_t s) {
   const int TSn = ceil_div(max_np, SF);
-  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, f, scratch, state,
-                                                                        nullptr);
-  k_symv_reduce_w<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, scratch, u, state, SF);
+  float2* P = reinterpret_cast<float2*>(scratch);
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, f, fsplit, state);
+  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, fsplit, P, state,
+                                                                        accurate);
+  k_symv_reduce_df<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, P, u, state);
   return cudaGetLastError();
 }
 

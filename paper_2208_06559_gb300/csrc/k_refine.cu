@@ -31,9 +31,21 @@ __device__ __forceinline__ void dfa_add_prod(DFa& a, float d, float xh, float xl
   a.lo += err + e + d * xl;
 }
 
-__device__ __forceinline__ double dwarp_sum(double v) {
+// a += b for double-float values (two-sum of the high parts)
+__device__ __forceinline__ void dfa_add(DFa& a, float bh, float bl) {
+  const float s = a.hi + bh;
+  const float bp = s - a.hi;
+  a.lo += ((a.hi - (s - bp)) + (bh - bp)) + bl;
+  a.hi = s;
+}
+
+__device__ __forceinline__ DFa dfa_warp_sum(DFa v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    dfa_add(v, h, l);
+  }
   return v;
 }
 
@@ -78,18 +90,20 @@ __global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
       dfa_add_prod(acc, v3, xh[c + 96], xl[c + 96]);
     }
     for (; c <= row; c += 32) dfa_add_prod(acc, Lr[c], xh[c], xl[c]);
-    const double t = dwarp_sum((double)acc.hi + (double)acc.lo);
-    if (lane == 0) y[3 * d.boff + row] = scale * t;
+    acc = dfa_warp_sum(acc);
+    if (lane == 0) y[3 * d.boff + row] = scale * ((double)acc.hi + (double)acc.lo);
   }
 }
 
 // z = Lt^{-T} x: one CTA (1024 threads) per chain, 128-row blocks from the
 // last to the first.  Thread t owns columns a = t, t + 1024, ...; after block
 // b is solved (z_b = W_bb^T (x_b - acc_b), W_bb the stored inverse of the
-// diagonal tile) every thread adds sum_{rho in b} Lt[rho][a] z_rho to its
-// columns a < 128 b: each row of Lt is read once, coalesced.
+// diagonal tile, staged in shared memory and applied by all 1024 threads,
+// eight partial sums per output) every thread adds sum_{rho in b} Lt[rho][a]
+// z_rho to its columns a < 128 b: each row of Lt is read once, coalesced.
 constexpr int kTrsvThreads = 1024;
 constexpr int kTrsvMaxCols = 12;  // np <= 12288 (N <= 4096)
+constexpr int kTrsvSmem = (kMixedTile * kMixedTile + 2 * 8 * kMixedTile) * 4;  // W_b, partials
 
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __restrict__ M,
                                                              const float* __restrict__ Winv,
@@ -97,7 +111,11 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __rest
                                                              const double* __restrict__ x_in,
                                                              const StepArgs* __restrict__ args,
                                                              double* __restrict__ z) {
-  __shared__ double sacc[128], sb[128];
+  extern __shared__ __align__(16) float tv_smem[];
+  float* Ws = tv_smem;                                  // [128][128] W_bb
+  float* ph = Ws + kMixedTile * kMixedTile;             // [8][128] partial hi
+  float* pl = ph + 8 * kMixedTile;                      // [8][128] partial lo
+  __shared__ double sacc[128];
   __shared__ float zh[128], zl[128], sh[128], sl[128];
   const ChainDesc d = cd[blockIdx.x];
   const int T = d.np / kMixedTile;
@@ -111,6 +129,11 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __rest
   for (int q = 0; q < kTrsvMaxCols; ++q) acc[q] = DFa{0.f, 0.f};
   for (int b = T - 1; b >= 0; --b) {
     const int c0 = 128 * b;
+    {  // stage W_bb (16 KB rows, coalesced float4)
+      const float4* Wg = reinterpret_cast<const float4*>(Winv + ((long long)d.wrow + c0) * kMixedTile);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(Ws)[t + kTrsvThreads * q] = __ldg(Wg + t + kTrsvThreads * q);
+    }
     // columns of block b owned by this thread: a = t + 1024 q in [c0, c0 + 128)
 #pragma unroll
     for (int q = 0; q < kTrsvMaxCols; ++q) {
@@ -121,15 +144,26 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __rest
     if (t < 128) {
       const int a = c0 + t;
       const double rhs = ((a < d.n) ? x[a] : 0.0) - sacc[t];
-      sb[t] = rhs;
       sh[t] = (float)rhs;
       sl[t] = (float)(rhs - (double)sh[t]);
     }
     __syncthreads();
-    if (t < 128) {  // z_i = sum_{j >= i} W[j][i] s_j
-      const float* W = Winv + ((long long)d.wrow + c0) * kMixedTile;
+    {  // z_i = sum_{j >= i} W[j][i] s_j: output i = t % 128, rows j in [16 p, 16 p + 16)
+      const int i = t & 127, p = t >> 7;
       DFa zi{0.f, 0.f};
-      for (int j = t; j < 128; ++j) dfa_add_prod(zi, W[j * kMixedTile + t], sh[j], sl[j]);
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = 16 * p + jj;
+        if (j >= i) dfa_add_prod(zi, Ws[j * kMixedTile + i], sh[j], sl[j]);
+      }
+      ph[p * kMixedTile + i] = zi.hi;
+      pl[p * kMixedTile + i] = zi.lo;
+    }
+    __syncthreads();
+    if (t < 128) {
+      DFa zi{ph[t], pl[t]};
+#pragma unroll
+      for (int p = 1; p < 8; ++p) dfa_add(zi, ph[p * kMixedTile + t], pl[p * kMixedTile + t]);
       const double v = (double)zi.hi + (double)zi.lo;
       zh[t] = (float)v;
       zl[t] = (float)(v - (double)zh[t]);
@@ -174,7 +208,8 @@ __global__ void k_refine_combine(const ChainDesc* __restrict__ cd, const double*
 cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
-                                double* scratch, cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev) {
+                                double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
+                                cudaEvent_t* ev) {
   k_split<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, x, args, scratch);
   if (!refine) {
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
@@ -184,15 +219,19 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
   cudaError_t e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
   if (e != cudaSuccess) return e;
-  k_trsv_t_f32<<<n_chains, kTrsvThreads, 0, s2>>>(M, Winv, cd, x, args, z);
+  k_trsv_t_f32<<<n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
   k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
   e = cudaEventRecord(ev[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e != cudaSuccess) return e;
-  e = launch_symv<float>(M, cd, n_chains, max_np, z, scratch, w, nullptr, s);
+  e = launch_symv_f32(M, cd, n_chains, max_np, z, fsplit, scratch, w, nullptr, nullptr, s);
   if (e != cudaSuccess) return e;
   k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);
   return cudaGetLastError();
+}
+
+cudaError_t refine_configure() {
+  return cudaFuncSetAttribute(k_trsv_t_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
 }
 
 }  // namespace bd
