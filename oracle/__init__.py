@@ -28,6 +28,7 @@ OK = 0
 ERR_NOT_PD = -4
 ERR_CONSTRAINT = -5
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
+RIGID, FRAENKEL = 0, 1
 OBS_STRIDE = 12
 
 
@@ -41,13 +42,15 @@ class Params(ctypes.Structure):
         ("lambda_", ctypes.c_double),
         ("tol", ctypes.c_double),
         ("max_newton", ctypes.c_int),
+        ("constraint", ctypes.c_int),
+        ("kspring", ctypes.c_double),
     ]
 
 
 def make_params(hstar=0.25, a=0.0, dt=1e-4, flow=FLOW_NONE, Wi=0.0, lam=1.0,
-                tol=1e-13, max_newton=50) -> Params:
+                tol=1e-13, max_newton=50, constraint=RIGID, kspring=0.0) -> Params:
     return Params(float(hstar), float(a), float(dt), int(flow), float(Wi),
-                  float(lam), float(tol), int(max_newton))
+                  float(lam), float(tol), int(max_newton), int(constraint), float(kspring))
 
 
 def build(force: bool = False) -> str:
@@ -87,6 +90,8 @@ def lib():
         L.or_run.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ip, dp, ctypes.c_int,
                              dp, dp, ip, ip, dp]
         L.or_observables.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_fraenkel_update.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                         dp, dp, dp, dp]
         L.or_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -201,6 +206,21 @@ def run(params: Params, Nc, r, noise):
     lib().or_run(ctypes.byref(params), nc, _i(Nc), _d(r), n_steps,
                  _d(noise) if n_steps else None, _d(T), _i(status), _i(iters), _d(maxdev))
     return r, T[: int(Nc.sum()) - nc], status, iters, maxdev
+
+
+def fraenkel_update(D, kappa_, dt, kspring, r, y):
+    """Semi-implicit Fraenkel-spring update (Sec. 3 eqQ2, Eqs. (23)-(25)) of
+    one chain from positions r and scaled Brownian displacement y.
+    Returns (r_new, T) with T_k = K* (|Q_k| - 1) / |Q_k| at the new links."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    kap = np.ascontiguousarray(kappa_, dtype=np.float64).reshape(9)
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 3)
+    N = r.shape[0]
+    rn = np.zeros_like(r)
+    T = np.zeros(max(N - 1, 1))
+    lib().or_fraenkel_update(N, _d(D), _d(kap), float(dt), float(kspring), _d(r), _d(y), _d(rn), _d(T))
+    return rn, T[: N - 1]
 
 
 def observables(r, T=None):

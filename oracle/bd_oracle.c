@@ -284,6 +284,35 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
     /* 3. Brownian displacement y = sqrt(2 dt) L xi (Eq. (6) noise term) */
     or_trmv_lower(n, L, xi, y);
     double s = sqrt(2.0 * p->dt);
+    if (p->constraint == OR_FRAENKEL) {
+      /* 4'. Fraenkel springs, semi-implicit link update (Sec. 3) */
+      for (int e = 0; e < n; ++e) y[e] *= s;
+      or_fraenkel_update(N, D, kap, p->dt, p->kspring, r, y, rn, T);
+      memcpy(r, rn, sizeof(double) * n);
+      if (T_out) memcpy(T_out, T, sizeof(double) * m);
+      if (iters) *iters = 0;
+      if (maxdev) {
+        double md = 0.0;
+        for (int k = 0; k < m; ++k) {
+          double q2 = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            double d = r[3 * (k + 1) + c] - r[3 * k + c];
+            q2 += d * d;
+          }
+          double dv = fabs(sqrt(q2) - 1.0);
+          if (dv > md) md = dv;
+        }
+        *maxdev = md;
+      }
+      free(D);
+      free(L);
+      free(y);
+      free(rs);
+      free(rn);
+      free(u);
+      free(T);
+      return OR_OK;
+    }
     /* 4. predictor r* = r + dt kappa.r + y (Eq. (6) flow term) and the old
      *    rod directions u_k = Q_k / |Q_k| along which tensions act */
     for (int i = 0; i < N; ++i)
@@ -331,6 +360,84 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
   free(u);
   free(T);
   return status;
+}
+
+/* Fraenkel springs, Sec. 3 Eq. (3): F_k = K* (|Q_k| - 1) Q_k / |Q_k|, the
+ * force that spring k exerts on bead k (and minus it on bead k + 1).  The
+ * semi-implicit scheme of Sec. 3 takes spring k's own contribution to link
+ * k implicitly:
+ *   eqQ2: Y_k = Q_k + [explicit change of link k with every spring force at
+ *         time t] + 2 dt F_k(t)  (the 2 dt F_k cancels the self term that
+ *         D_kk = D_k+1,k+1 = I gives to the explicit change);
+ *   Eq. (25): |Q_k'| = (2 dt K* + |Y_k|) / (2 dt K* + 1);
+ *   Eq. (23): Q_k' = Y_k |Q_k'| / |Y_k|  (Q_k' parallel to Y_k).
+ * The explicit change of the bead positions is the Euler step of Eq. (6):
+ * dr_i = dt (kappa . r_i + sum_j D_ij Fb_j) + y_i, with the bead forces
+ * Fb_i = F_i - F_{i-1}. */
+void or_fraenkel_update(int N, const double* D, const double* kappa, double dt, double kspring,
+                        const double* r, const double* y, double* r_new, double* T_out) {
+  int n = 3 * N, m = N - 1;
+  double* Fs = (double*)calloc(3 * (size_t)(m > 0 ? m : 1), sizeof(double));
+  double* Fb = (double*)calloc((size_t)n, sizeof(double));
+  double* v = (double*)calloc((size_t)n, sizeof(double));
+  double* dr = (double*)calloc((size_t)n, sizeof(double));
+  double* rp = (double*)calloc((size_t)n, sizeof(double));
+  /* spring forces at time t and the bead forces */
+  for (int k = 0; k < m; ++k) {
+    double q[3], qn = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      q[c] = r[3 * (k + 1) + c] - r[3 * k + c];
+      qn += q[c] * q[c];
+    }
+    qn = sqrt(qn);
+    for (int c = 0; c < 3; ++c) Fs[3 * k + c] = kspring * (qn - 1.0) / qn * q[c];
+  }
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < 3; ++c) {
+      double f = 0.0;
+      if (i < m) f += Fs[3 * i + c];
+      if (i > 0) f -= Fs[3 * (i - 1) + c];
+      Fb[3 * i + c] = f;
+    }
+  /* explicit bead step */
+  or_gemv(n, D, Fb, v);
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < 3; ++c) {
+      double kr = kappa[3 * c] * r[3 * i] + kappa[3 * c + 1] * r[3 * i + 1] + kappa[3 * c + 2] * r[3 * i + 2];
+      dr[3 * i + c] = dt * (kr + v[3 * i + c]) + y[3 * i + c];
+    }
+  /* new links (eqQ2, Eqs. (25), (23)) summed from bead 0 */
+  for (int c = 0; c < 3; ++c) rp[c] = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double Y[3], yn = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      Y[c] = (r[3 * (k + 1) + c] - r[3 * k + c]) + (dr[3 * (k + 1) + c] - dr[3 * k + c]) +
+             2.0 * dt * Fs[3 * k + c];
+      yn += Y[c] * Y[c];
+    }
+    yn = sqrt(yn);
+    double qn = (2.0 * dt * kspring + yn) / (2.0 * dt * kspring + 1.0);
+    for (int c = 0; c < 3; ++c) rp[3 * (k + 1) + c] = rp[3 * k + c] + Y[c] * (qn / yn);
+    if (T_out) T_out[k] = kspring * (qn - 1.0) / qn;
+  }
+  /* centre of mass: old centre plus the mean explicit displacement */
+  for (int c = 0; c < 3; ++c) {
+    double cm_old = 0.0, mdr = 0.0, mrp = 0.0;
+    for (int i = 0; i < N; ++i) {
+      cm_old += r[3 * i + c];
+      mdr += dr[3 * i + c];
+      mrp += rp[3 * i + c];
+    }
+    cm_old /= N;
+    mdr /= N;
+    mrp /= N;
+    for (int i = 0; i < N; ++i) r_new[3 * i + c] = rp[3 * i + c] - mrp + cm_old + mdr;
+  }
+  free(Fs);
+  free(Fb);
+  free(v);
+  free(dr);
+  free(rp);
 }
 
 void or_run(const or_params* p, int n_chains, const int* Nc, double* r,

@@ -35,6 +35,9 @@ extern "C" {
 #define OR_FLOW_SHEAR 1
 #define OR_FLOW_UNIAXIAL 2
 
+#define OR_RIGID 0    /* rigid rods: tension solve */
+#define OR_FRAENKEL 1 /* Fraenkel springs of stiffness kspring, semi-implicit (Sec. 3) */
+
 #define OR_OBS_STRIDE 12 /* Rx Ry Rz R2 Rg2 stretch max||Q|-1| newton_iters tau_xx tau_yy tau_zz tau_xy */
 
 typedef struct {
@@ -46,6 +49,8 @@ typedef struct {
   double lambda;   /* relaxation time; rate = Wi / lambda; <= 0 means 1 */
   double tol;      /* Newton tolerance on max_k | |Q_k|^2 - 1 | */
   int max_newton;  /* Newton update cap */
+  int constraint;  /* OR_RIGID or OR_FRAENKEL */
+  double kspring;  /* Fraenkel spring constant K* (OR_FRAENKEL) */
 } or_params;
 
 /* 3x3 RPY block for separation R = r_i - r_j, Sec. 3 Eqs. (8)-(9). */
@@ -72,8 +77,17 @@ int or_tension_solve(int N, const double* D, const double* rstar,
                      const double* u, double dt, double tol, int max_newton,
                      double* T, double* r_out, int* iters);
 
+/* Semi-implicit Fraenkel-spring update of one chain (Sec. 3, Eq. (3) and
+ * the link equations eqQ2, (23)-(25)): from the old positions r, the
+ * scaled Brownian displacement y (= sqrt(2 dt) L xi), kappa and D, the new
+ * positions r_new; T_out[k] = K* (|Q_k| - 1) / |Q_k| at the new links (the
+ * spring force is T_out[k] Q_k).  The centre of mass moves with the
+ * explicit step; the new links are summed around it. */
+void or_fraenkel_update(int N, const double* D, const double* kappa, double dt, double kspring,
+                        const double* r, const double* y, double* r_new, double* T_out);
+
 /* One full time step for one chain (assembly, Cholesky, Brownian
- * displacement, flow predictor, tension solve).  r is updated in place
+ * displacement, flow predictor, tension solve or Fraenkel update).  r is updated in place
  * unless the step fails, in which case r is left unchanged.
  * T_out (N-1) may be NULL.  Returns 0 or an error code. */
 int or_step(const or_params* p, int N, double* r, const double* xi,

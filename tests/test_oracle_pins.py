@@ -454,3 +454,104 @@ def test_dumbbell_stress_in_extension():
     r1, T, st, it, md = orc.step(p, np.array([[0.0, 0, 0], [1.0, 0, 0]]), np.zeros((2, 3)))
     o = orc.observables(r1, T)
     np.testing.assert_allclose(o[8] - o[9], rate / (2 * (1 - mu_far(1.0, 0.25, 0.25)[0])), rtol=1e-12)
+
+
+# ------------------------------------------------ Fraenkel springs (Sec. 3)
+def _fraenkel_params(**kw):
+    base = dict(hstar=0.25, a=0.25, dt=1e-3, constraint=orc.FRAENKEL, kspring=1000.0)
+    base.update(kw)
+    return orc.make_params(**base)
+
+
+def test_fraenkel_zero_stiffness_is_the_explicit_euler_step():
+    """With K* = 0 there is no spring force and the semi-implicit update
+    reduces to the explicit step r + dt kappa.r + y of Eq. (6): this checks
+    the link update and the reconstruction of positions around the centre of
+    mass together."""
+    r = inputs.random_walk([9], 41)
+    y = 1e-2 * inputs.gaussian_noise(1, 9, 42)[0]
+    D = orc.assemble(r, 0.25, 0.25)
+    kap = orc.kappa(orc.FLOW_SHEAR, 3.0)
+    rn, T = orc.fraenkel_update(D, kap, 1e-3, 0.0, r, y)
+    np.testing.assert_allclose(rn, r + 1e-3 * r @ kap.T + y, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(T, 0.0)
+
+
+def test_fraenkel_free_draining_dumbbell_is_backward_euler():
+    """h* = 0, no noise, no flow: the bond length of a dumbbell follows the
+    backward-Euler step of dL/dt = -2 K* (L - 1), so after n steps
+    L_n - 1 = (L_0 - 1) / (1 + 2 dt K*)^n, and the bond keeps its direction."""
+    K, dt, L0, n = 50.0, 1e-3, 1.7, 25
+    d = np.array([0.3, -0.4, np.sqrt(1 - 0.25)])
+    r = np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3]]) + np.vstack([np.zeros(3), L0 * d])
+    p = _fraenkel_params(hstar=0.0, a=0.0, dt=dt, kspring=K)
+    rr, T, st, it, md = orc.run(p, np.array([2], np.int32), r, np.zeros((n, 2, 3)))
+    Q = rr[1] - rr[0]
+    L = np.linalg.norm(Q)
+    np.testing.assert_allclose(L - 1.0, (L0 - 1.0) / (1.0 + 2 * dt * K) ** n, rtol=1e-12)
+    np.testing.assert_allclose(Q / L, d, atol=1e-14)
+    np.testing.assert_allclose(rr.mean(0), r.mean(0), atol=1e-14)  # no net force, no drift
+    np.testing.assert_allclose(T[0], K * (L - 1) / L, rtol=1e-12)
+
+
+def test_fraenkel_dumbbell_with_hi_one_step():
+    """With HI the coupling D_01 = mu_par along the bond stays explicit:
+    |Y| = L_0 + 2 dt mu_par K* (L_0 - 1), and |Q'| = (2 dt K* + |Y|) / (2 dt K* + 1)
+    (Eq. (25)), with mu_par the parallel RPY coefficient at R = L_0."""
+    K, dt, L0, hs = 100.0, 1e-3, 1.5, 0.25
+    r = np.array([[0.0, 0.0, 0.0], [L0, 0.0, 0.0]])
+    mu_par = orc.rpy_block(np.array([L0, 0.0, 0.0]), hs, hs)[0, 0]
+    # closed form of the far-field RPY parallel coefficient (Eq. (8)) as a cross-check
+    np.testing.assert_allclose(mu_par, 0.75 * hs / L0 * (2 - 4 * hs * hs / (3 * L0 * L0)), rtol=1e-14)
+    p = _fraenkel_params(hstar=hs, a=hs, dt=dt, kspring=K)
+    rr, T, st, it, md = orc.run(p, np.array([2], np.int32), r, np.zeros((1, 2, 3)))
+    Y = L0 + 2 * dt * mu_par * K * (L0 - 1)
+    np.testing.assert_allclose(np.linalg.norm(rr[1] - rr[0]), (2 * dt * K + Y) / (2 * dt * K + 1), rtol=1e-13)
+
+
+def test_fraenkel_stiff_limit_holds_unit_links():
+    """K* -> infinity: |Q'| = (2 dt K* + |Y|) / (2 dt K* + 1) -> 1 for every link."""
+    Nc = np.array([30], np.int32)
+    r = inputs.random_walk(Nc, 43)
+    p = _fraenkel_params(dt=1e-4, kspring=1e13)
+    rr, T, st, it, md = orc.run(p, Nc, r, inputs.gaussian_noise(5, 30, 44))
+    Q = np.linalg.norm(np.diff(rr, axis=0), axis=1)
+    assert np.abs(Q - 1).max() < 1e-8
+
+
+def _fraenkel_q2(K):
+    """<|Q|^2> for the Fraenkel spring's Boltzmann weight Q^2 exp(-K (Q-1)^2 / 2)."""
+    q = np.linspace(max(0.0, 1 - 12 / np.sqrt(K)), 1 + 12 / np.sqrt(K), 20001)
+    w = q * q * np.exp(-0.5 * K * (q - 1) ** 2)
+    return float((w * q * q).sum() / w.sum())
+
+
+@pytest.mark.parametrize("hs", [0.0, 0.25])
+def test_fraenkel_equilibrium_statics(hs):
+    """Stiff springs (K* = 1000, dt = 1e-3, the paper's equilibrium settings):
+    <R^2> = (N-1) <Q^2> and <Q_k . Q_k+1> = 0 within 3 s.e., with and without
+    HI (RPY is divergence free, so the statics do not depend on h*)."""
+    N, n_chains, K = 4, 1500, 1000.0
+    p = _fraenkel_params(hstar=hs, a=0.25 if hs > 0 else 0.0, kspring=K)
+    Nc = np.full(n_chains, N, np.int32)
+    r = inputs.random_walk(Nc, 45 + int(hs * 100))
+    key = [46]
+
+    def adv(r, steps):
+        r, T, st, it, md = orc.run(p, Nc, r, inputs.gaussian_noise(steps, n_chains * N, key[0]))
+        key[0] += 1
+        assert np.all(st == 0)
+        return r
+
+    r = adv(r, 1000)
+    R2, cs = [], []
+    for _ in range(8):
+        r = adv(r, 500)
+        rr = r.reshape(n_chains, N, 3)
+        R = rr[:, -1] - rr[:, 0]
+        R2.append((R * R).sum(1))
+        Q = np.diff(rr, axis=1)
+        cs.append((Q[:, :-1] * Q[:, 1:]).sum(2).mean(1))
+    R2, cs = np.mean(R2, axis=0), np.mean(cs, axis=0)
+    assert abs(R2.mean() - (N - 1) * _fraenkel_q2(K)) < 3 * _se(R2)
+    assert abs(cs.mean()) < 3 * _se(cs)
