@@ -134,6 +134,19 @@ int bd_observables(bd_ctx* ctx, double* obs, int* status_host, void* stream);
  * returns the most severe status. */
 int bd_chain_status(bd_ctx* ctx, int* status_host, int* newton_host, void* stream);
 
+/* One time step launched kernel by kernel (no graph) with CUDA events at the
+ * stage boundaries, for profiling.  noise: device pointer, [sum N][3] FP64,
+ * the step's N(0,1) noise; newton_iters: tension-solve bodies enqueued
+ * (<= 0: max_newton + 2; chains that have converged skip them on the
+ * device).  ms_out[8] (host) receives milliseconds: assembly, Cholesky
+ * factorisation, Brownian displacement, wait for the rod-coupling matrix K
+ * (built on a second stream) plus the predictor, tension iterations,
+ * commit, whole step, and the end of the K chain measured from the start of
+ * the step.  The state advances by one step as with bd_step.  Synchronises
+ * the context's stream.  Errors: BD_ERR_ARG (NULL or host noise),
+ * BD_ERR_STATE (no state), BD_ERR_CUDA. */
+int bd_profile_step(bd_ctx* ctx, const double* noise, int newton_iters, double* ms_out);
+
 /* Number of kernel launches executed by bd_step on this context since its
  * creation (the captured step graph's kernels times the steps, plus the
  * kernels of every executed tension-solve iteration).  Synchronises the

@@ -78,6 +78,8 @@ EXPORTS = {
     "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bd_kernel_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.c_void_p]),
+    "bd_profile_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]),
     "bd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_void_p]),
@@ -233,6 +235,17 @@ class Context:
         _check(lib().bd_kernel_launches(self._h, ctypes.byref(v), _stream(stream)),
                "bd_kernel_launches")
         return int(v.value)
+
+    PROFILE_STAGES = ("assemble", "factor", "brownian", "k_wait_predictor", "tension",
+                      "commit", "step", "k_chain_end")
+
+    def profile_step(self, noise, newton_iters: int = 0) -> dict:
+        """One step launched kernel by kernel with stage-boundary events:
+        {stage: ms}, keys PROFILE_STAGES (k_chain_end from the step start)."""
+        assert noise.is_cuda and noise.is_contiguous()
+        out = (ctypes.c_double * 8)()
+        _check(lib().bd_profile_step(self._h, _ptr(noise), int(newton_iters), out), "bd_profile_step")
+        return dict(zip(self.PROFILE_STAGES, list(out)))
 
     def adjoint(self, r0, noise, dJdr_final, ckpt_every: int = 20, stream=None):
         """(dJ/dWi, dJ/dh*) at fixed noise for J with gradient dJdr_final at the

@@ -87,11 +87,16 @@ template <typename T>
 cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_np,
                         const double* f, double* scratch, double* u, const int* state,
                         cudaStream_t s);
-// FP32-storage mobility product with a per-chain accuracy switch (see
-// k_matvec.cu).  fsplit: [sum np] float2, scratch: the two-phase partials.
+// Per-chain mode of the FP32-storage mobility product inside the tension
+// iteration (k_matvec.cu): the full product u = D f or the increment
+// u += D df, in plain FP32 or in compensated (double-float) FP32.
+enum MobMode : int { MOB_FULL_F32 = 0, MOB_FULL_DF = 1, MOB_INC_DF = 2, MOB_INC_F32 = 3 };
+// FP32-storage mobility product.  fsplit: [sum np] float2; scratch: the
+// two-phase partials; mode: per chain (NULL = full product, double-float;
+// df unused then).
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, float2* fsplit, double* scratch, double* u,
-                            const int* state, const int* accurate, cudaStream_t s);
+                            const double* f, const double* df, float2* fsplit, double* scratch,
+                            double* u, const int* state, const int* mode, cudaStream_t s);
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s);
@@ -108,13 +113,14 @@ cudaError_t launch_newton_residual(const double* rstar, const double* u, const C
                                    int n_chains, Phys ph, double* rT, double* rhs,
                                    int* state, int* status, const int* iters, int* accurate,
                                    cudaStream_t s);
+// dF (optional): F(delta), the change of the forces, for incremental products.
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F,
-                                int* state, int* iters, cudaStream_t s);
+                                int* state, int* iters, cudaStream_t s, double* dF = nullptr);
 cudaError_t launch_newton_any_active(const int* state, int n_chains,
                                      cudaGraphConditionalHandle h, unsigned long long* loops,
-                                     StepArgs* args, int max_loops, cudaStream_t s);
+                                     StepArgs* args, int max_loops, bool count, cudaStream_t s);
 cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_beads,
                             const double* rT, double* r, const int* state, int* status,
                             StepArgs* args, cudaStream_t s);
@@ -132,6 +138,11 @@ cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_ch
 cudaError_t matvec_configure();
 cudaError_t assemble_configure();
 cudaError_t tension_configure();
+// Kernels of the rod-coupling-matrix chain (K formation and factorisation),
+// for per-node priorities in the captured step graph.
+const void* form_k_kernel(bool fp32);
+bool is_k64_kernel(const void* f);
+const void* rod_dirs_kernel();
 cudaError_t refine_configure();
 
 // Mixed-precision Brownian displacement with one refinement step (k_refine.cu):

@@ -44,18 +44,20 @@ struct bd_ctx {
   double *uhat = nullptr, *T = nullptr, *rhs = nullptr, *scratch = nullptr, *obs = nullptr;
   float* Winv = nullptr;           // mixed: inverses of the diagonal tiles, [sum np][128]
   float2* fsplit = nullptr;        // mixed: (hi, lo) split of a mobility product's input, [sum np]
+  double* dF = nullptr;            // mixed: change of the forces in the last tension update
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
   CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
   double* stage = nullptr;  // staging for host-memory noise / observables
   size_t stage_elems = 0;
   int *status = nullptr, *state = nullptr, *iters = nullptr;
-  int* accurate = nullptr;  // mixed: per chain, 1 once the tension residual needs FP64-level sums
+  int* accurate = nullptr;  // mixed: per chain, mode of the tension iteration's mobility product (MobMode)
   StepArgs* args = nullptr;
   unsigned long long* loops = nullptr;  // Newton loop-body executions (device counter)
   unsigned long long steps_launched = 0;
   size_t graph_kernels = 0, body_kernels = 0;
   cudaStream_t cs = nullptr, cs2 = nullptr;
+  int pr_high = 0, pr_low = 0;  // highest (numerically lowest) and lowest stream priorities
   // mixed factorisation: chain groups on their own streams, so that one
   // group's latency-bound diagonal-tile step overlaps another's products
   static constexpr int kMaxGroups = 8;
@@ -76,6 +78,9 @@ struct bd_ctx {
   double *Tdot = nullptr, *Fdot = nullptr, *rscale = nullptr, *kdot = nullptr;
   bool have_state = false;
   int direct_iters = 0;  // > 0: launch the step's kernels directly (profiling), no graph
+  int graph_unroll = 0;  // tension iterations captured as plain graph nodes before the WHILE node
+  int while_cap = 1;     // WHILE-node iterations allowed per step
+  cudaEvent_t* prof = nullptr;  // bd_profile_step: stage-boundary events
   std::mutex mu;
 };
 
@@ -155,12 +160,17 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
 
 int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->fsplit, c->scratch,
-                       u, state, nullptr, s));
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, nullptr, c->fsplit,
+                       c->scratch, u, state, nullptr, s));
   else
     CK(launch_symv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
                            state, s));
   return BD_OK;
+}
+
+// Stage-boundary event for bd_profile_step (no-op otherwise).
+void prof_mark(bd_ctx* c, int i, cudaStream_t s) {
+  if (c->prof) cudaEventRecord(c->prof[i], s);
 }
 
 // Before the tension solve.  The K chain (rod directions, K, its factor)
@@ -169,6 +179,7 @@ int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaSt
 int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   int rc;
   if ((rc = enqueue_assemble(c, s))) return rc;
+  prof_mark(c, 1, s);
   cudaStream_t sk = c->aux[0];
   CK(cudaEventRecord(c->aev[0], s));
   CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
@@ -184,12 +195,16 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
     CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
                                 c->max_mp / kSimtTile, true, c->status, sk));
   }
+  prof_mark(c, 7, sk);
   CK(cudaEventRecord(c->aev[1], sk));
   if ((rc = enqueue_factor(c, s))) return rc;
+  prof_mark(c, 2, s);
   if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
+  prof_mark(c, 3, s);
   CK(cudaStreamWaitEvent(s, c->aev[1], 0));
   CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
                       c->F, c->state, c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
+  prof_mark(c, 4, s);
   return BD_OK;
 }
 
@@ -197,25 +212,33 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
 // sums while a chain's residual is large, compensated (FP64-level) after.
 int enqueue_newton_symv(bd_ctx* c, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->fsplit,
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->dF, c->fsplit,
                        c->scratch, c->u, c->state, c->accurate, s));
   else
     return enqueue_symv(c, c->F, c->u, c->state, s);
   return BD_OK;
 }
 
-int enqueue_newton_body(bd_ctx* c, cudaGraphConditionalHandle h, cudaStream_t s) {
+// One tension iteration: mobility product, residual and state update, solve.
+int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
   int rc;
   if ((rc = enqueue_newton_symv(c, s))) return rc;
   CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
                             c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
   if (c->mixed)
-    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
-                                  c->T, c->F, c->state, c->iters, s));
+    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph,
+                                  c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s, c->dF));
   else
-    CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat,
-                                   c->rhs, c->T, c->F, c->state, c->iters, s));
-  CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->ph.max_newton + 3, s));
+    CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph,
+                                   c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
+  return BD_OK;
+}
+
+// Body of the WHILE node: one iteration, then the loop condition.
+int enqueue_newton_body(bd_ctx* c, cudaGraphConditionalHandle h, cudaStream_t s) {
+  int rc;
+  if ((rc = enqueue_newton_iter(c, s))) return rc;
+  CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->while_cap, true, s));
   return BD_OK;
 }
 
@@ -232,11 +255,40 @@ size_t count_kernel_nodes(cudaGraph_t g) {
   return k;
 }
 
+// Kernel nodes of a captured graph keep no stream priority: the K chain's
+// nodes get the lowest priority, every other kernel the highest (mixed path;
+// the FP64 path shares its tile kernels between both chains and keeps them
+// all high).
+void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+    const bool kchain = c->mixed && (kp.func == form_k_kernel(true) || kp.func == rod_dirs_kernel() ||
+                                     is_k64_kernel(kp.func));
+    cudaLaunchAttributeValue v;
+    memset(&v, 0, sizeof(v));
+    v.priority = kchain ? c->pr_low : c->pr_high;
+    cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v);
+  }
+  cudaGetLastError();
+}
+
 int build_step_graph(bd_ctx* c) {
   if (c->exec) return BD_OK;
   cudaStream_t s = c->cs;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = enqueue_pre_newton(c, s);
+  // the first graph_unroll tension iterations are plain nodes (chains that
+  // have converged skip them on the device); the WHILE node takes the rest
+  for (int i = 0; rc == BD_OK && i < c->graph_unroll; ++i) rc = enqueue_newton_iter(c, s);
+  c->while_cap = c->ph.max_newton + 3 - c->graph_unroll;
+  if (c->while_cap < 1) c->while_cap = 1;
   cudaGraph_t g = nullptr;
   if (rc) {
     cudaStreamEndCapture(s, &g);
@@ -249,7 +301,12 @@ int build_step_graph(bd_ctx* c) {
   cudaGraph_t cg = nullptr;
   CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
   cudaGraphConditionalHandle h;
-  CK(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&h, cg, c->graph_unroll > 0 ? 0 : 1, cudaGraphCondAssignDefault));
+  if (c->graph_unroll > 0) {
+    // enter the loop only if a chain is still iterating
+    CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->while_cap, false, s));
+    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+  }
   // cudaGraphNodeParams holds a union without a default constructor
   alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
   memset(cp_buf, 0, sizeof(cp_buf));
@@ -275,10 +332,12 @@ int build_step_graph(bd_ctx* c) {
   CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
                      c->args, s));
   CK(cudaStreamEndCapture(s, &g));
+  set_graph_priorities(c, g);
+  set_graph_priorities(c, body);
   c->graph = g;
   c->graph_kernels = count_kernel_nodes(g);
   c->body_kernels = count_kernel_nodes(body);
-  CK(cudaGraphInstantiate(&c->exec, g, 0));
+  CK(cudaGraphInstantiate(&c->exec, g, cudaGraphInstantiateFlagUseNodePriority));
   return BD_OK;
 }
 
@@ -287,20 +346,14 @@ int build_step_graph(bd_ctx* c) {
 // enqueued a fixed number of times (converged chains skip it on the device).
 int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
   int rc;
+  prof_mark(c, 0, s);
   if ((rc = enqueue_pre_newton(c, s))) return rc;
-  for (int it = 0; it < c->direct_iters; ++it) {
-    if ((rc = enqueue_newton_symv(c, s))) return rc;
-    CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                              c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
-    if (c->mixed)
-      CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs,
-                                    c->T, c->F, c->state, c->iters, s));
-    else
-      CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph, c->uhat,
-                                     c->rhs, c->T, c->F, c->state, c->iters, s));
-  }
+  for (int it = 0; it < c->direct_iters; ++it)
+    if ((rc = enqueue_newton_iter(c, s))) return rc;
+  prof_mark(c, 5, s);
   CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
                      c->args, s));
+  prof_mark(c, 6, s);
   return BD_OK;
 }
 
@@ -427,7 +480,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dF, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -492,6 +545,13 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (const char* e = getenv("BD_STEP_DIRECT")) {
     const int v = atoi(e);
     c->direct_iters = v > 0 ? (v == 1 ? ph.max_newton + 2 : v) : 0;
+  }
+  // typical steps need 7-10 tension iterations: the first 8 are plain graph
+  // nodes, the WHILE node runs the rest
+  c->graph_unroll = ph.max_newton + 2 < 8 ? ph.max_newton + 2 : 8;
+  if (const char* e = getenv("BD_GRAPH_UNROLL")) {
+    const int v = atoi(e);
+    c->graph_unroll = v < 0 ? 0 : (v > ph.max_newton + 2 ? ph.max_newton + 2 : v);
   }
 
   long long boff = 0, roff = 0, moff = 0, koff = 0, soff = 0, wrow = 0, swrow = 0, kwrow = 0;
@@ -561,7 +621,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
        (c->mixed || alloc(&c->Minv, (size_t)swrow * kSimtTile * c->elem));
   if (ok && c->mixed)
     ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
-         alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) &&
+         alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) && alloc((void**)&c->dF, b3) &&
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
@@ -571,10 +631,19 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     bd_destroy(c);
     return code;
   };
-  if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking) != cudaSuccess)
+  // Stream priorities: the factorisation's latency-bound chain (main and
+  // chain-group streams) and the refinement's triangular solve go first; the
+  // rod-coupling matrix K, needed only after the Brownian displacement, is
+  // built at the lowest priority so that its bulk kernels fill idle SMs
+  // instead of delaying the diagonal tiles.
+  int pr_low = 0, pr_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&pr_low, &pr_high) != cudaSuccess) pr_low = pr_high = 0;
+  c->pr_high = pr_high;
+  c->pr_low = pr_low;
+  if (cudaStreamCreateWithPriority(&c->cs, cudaStreamNonBlocking, pr_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->cs2, cudaStreamNonBlocking, pr_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->aux[0], cudaStreamNonBlocking, pr_low) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, pr_high) != cudaSuccess)
     return fail(BD_ERR_CUDA);
   for (int g = 0; g < 4; ++g)
     if (cudaEventCreateWithFlags(&c->aev[g], cudaEventDisableTiming) != cudaSuccess)
@@ -583,7 +652,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (c->mixed) {
     set_groups(c, c->n_chains / 16);
     for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
-      if (cudaStreamCreateWithFlags(&c->gs[g], cudaStreamNonBlocking) != cudaSuccess)
+      if (cudaStreamCreateWithPriority(&c->gs[g], cudaStreamNonBlocking, c->pr_high) != cudaSuccess)
         return fail(BD_ERR_CUDA);
     for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
       if (cudaEventCreateWithFlags(&c->gev[g], cudaEventDisableTiming) != cudaSuccess)
@@ -671,6 +740,44 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
   for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, s));
   c->steps_launched += (unsigned long long)n_steps;
   return BD_OK;
+}
+
+int bd_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms_out) {
+  if (!c || !noise || !ms_out || !is_device_ptr(noise)) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = c->cs;
+  cudaEvent_t ev[8];
+  int made = 0;
+  for (; made < 8; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  int rc = BD_OK;
+  const int saved = c->direct_iters;
+  if (made < 8) {
+    rc = BD_ERR_CUDA;
+  } else {
+    c->prof = ev;
+    c->direct_iters = newton_iters > 0 ? newton_iters : c->ph.max_newton + 2;
+    const long long stride = c->total_beads * 3;
+    if (launch_set_args(c->args, noise, stride, s) != cudaSuccess) rc = BD_ERR_CUDA;
+    if (rc == BD_OK) rc = enqueue_step_direct(c, s);
+    if (rc == BD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BD_ERR_CUDA;
+    c->prof = nullptr;
+    c->direct_iters = saved;
+    if (rc == BD_OK) {
+      float t;
+      const int seg[7][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {0, 6}};
+      for (int k = 0; k < 7; ++k) {
+        if (cudaEventElapsedTime(&t, ev[seg[k][0]], ev[seg[k][1]]) != cudaSuccess) rc = BD_ERR_CUDA;
+        ms_out[k] = t;
+      }
+      if (cudaEventElapsedTime(&t, ev[0], ev[7]) != cudaSuccess) rc = BD_ERR_CUDA;
+      ms_out[7] = t;
+    }
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  return rc;
 }
 
 int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {

@@ -102,6 +102,10 @@ __global__ void __launch_bounds__(256) k_gemm64(float* __restrict__ K, const flo
 
 cudaError_t k64_configure() { return cudaSuccess; }
 
+bool is_k64_kernel(const void* f) {
+  return f == (const void*)k_potrf64 || f == (const void*)k_gemm64<true> || f == (const void*)k_gemm64<false>;
+}
+
 cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
                             int* status, cudaStream_t s) {
   for (int k = 0; k < max_tiles; ++k) {

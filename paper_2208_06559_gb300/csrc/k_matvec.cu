@@ -189,15 +189,24 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
   // R[x][y] = U[3*32*lt + x][3*32*kt + y]: rows from the l side (smaller bead
   // indices), columns from the k side; only entries with row < col are D.
   const int row0 = 3 * KR * lt, col0 = 3 * KR * kt;
+  // every element copied asynchronously (zero-filled outside the strict
+  // upper triangle), so all of a thread's loads are in flight at once
   for (int x = threadIdx.x >> 5; x < KE; x += 8) {
     const int rr = row0 + x;
     for (int y = threadIdx.x & 31; y < KE; y += 32) {
       const int cc = col0 + y;
-      T v = T(0);
-      if (rr < d.n && cc < d.n && rr < cc) v = base[(long long)rr * np + cc];
-      R[x][y] = v;
+      const bool in = rr < d.n && cc < d.n && rr < cc;
+      const T* src = in ? base + (long long)rr * np + cc : base;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(&R[x][y]);
+      if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(in ? 4 : 0)
+                     : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(in ? 8 : 0)
+                     : "memory");
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   if (threadIdx.x < KR) {
     const int t = threadIdx.x;
 #pragma unroll
@@ -206,6 +215,7 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
       ul[t][q] = (KR * lt + t < m) ? (T)uhat[3 * (d.roff + KR * lt + t) + q] : T(0);
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // D_ab v for bead a on the k side (a = 32 kt + ia), b on the l side
   // (b = 32 lt + ib), ia, ib in [0, 32].
@@ -314,127 +324,172 @@ __device__ __forceinline__ void upper_tile_of(int p, int& bi, int& bj) {
 }
 
 __global__ void k_split_f2(const ChainDesc* __restrict__ cd, const double* __restrict__ f,
-                           float2* __restrict__ fs, const int* __restrict__ state) {
+                           const double* __restrict__ df, float2* __restrict__ fs,
+                           const int* __restrict__ state, const int* __restrict__ mode) {
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.np) return;
-  const double v = (e < d.n) ? f[3 * d.boff + e] : 0.0;
+  const double* src = (mode && mode[c] >= MOB_INC_DF) ? df : f;
+  const double v = (e < d.n) ? src[3 * d.boff + e] : 0.0;
   const float h = (float)v;
   fs[d.swrow + e] = make_float2(h, (float)(v - (double)h));
 }
 
-// `accurate` (per chain, may be NULL = always): 0 selects plain FP32 sums
-// (relative error ~1e-7), used by the tension iteration while its residual
-// is still large.
+// Asynchronous 16- and 8-byte global -> shared copies (cp.async), grouped.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+constexpr int kSymvCtasPerSm = 5;
+
+// Tile `id` of the batch (chain-major, tpc tiles per chain slot): its chain,
+// block row and column; false if the chain has fewer tiles or is not active.
+__device__ __forceinline__ bool symv_tile(int id, int tpc, const ChainDesc* __restrict__ cd,
+                                          const int* __restrict__ state, int& c, int& bi, int& bj) {
+  c = id / tpc;
+  const int p = id - c * tpc;
+  if (state && state[c] >= NS_DONE) return false;
+  const int TSn = (cd[c].n + SF - 1) / SF;
+  if (p >= TSn * (TSn + 1) / 2) return false;
+  upper_tile_of(p, bi, bj);
+  return true;
+}
+
+// Persistent: CTA b takes tiles b, b + grid, ...; the next tile (and its two
+// f segments) is copied into the other shared-memory stage while the current
+// one is summed.  `mode` (per chain, may be NULL = double-float):
+// MOB_FULL_F32 and MOB_INC_F32 select plain FP32 sums (relative error ~1e-7),
+// used by the tension iteration while its residual is large, and for
+// increments once they are small.
 __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict__ M,
-                                                        const ChainDesc* __restrict__ cd,
-                                                        const float2* __restrict__ fs,
+                                                        const ChainDesc* __restrict__ cd, int n_chains,
+                                                        int tpc, const float2* __restrict__ fs,
                                                         float2* __restrict__ P,
                                                         const int* __restrict__ state,
-                                                        const int* __restrict__ accurate) {
-  __shared__ __align__(16) float S[SF][SFP];
-  __shared__ __align__(16) float frh[SF], frl[SF], fch[SF], fcl[SF];
-  const int c = blockIdx.y;
-  if (state && state[c] >= NS_DONE) return;
-  const ChainDesc d = cd[c];
-  const int TSn = (d.n + SF - 1) / SF;
-  const int p = blockIdx.x;
-  if (p >= TSn * (TSn + 1) / 2) return;
-  int bi, bj;
-  upper_tile_of(p, bi, bj);
-  const bool diag = (bi == bj);
-  const int r0 = bi * SF, c0 = bj * SF;
-  const float* base = M + d.moff + (long long)r0 * d.np + c0;
-  const long long np = d.np;
+                                                        const int* __restrict__ mode) {
+  __shared__ __align__(16) float S[2][SF][SFP];
+  __shared__ __align__(16) float2 fr[2][SF], fc[2][SF];  // (hi, lo) of f at the tile's rows / columns
   const int t = threadIdx.x;
-  // rows r0 .. r0 + 63 and columns c0 .. c0 + 63 lie inside the padded matrix
+  const int total = n_chains * tpc;
+  auto issue = [&](int id, int buf) {
+    int c, bi, bj;
+    if (id < total && symv_tile(id, tpc, cd, state, c, bi, bj)) {
+      const ChainDesc& d = cd[c];
+      const float* base = M + d.moff + (long long)(bi * SF) * d.np + bj * SF;
 #pragma unroll
-  for (int q = 0; q < SF * SF / 4 / 128; ++q) {
-    const int e = t + 128 * q;
-    const int r = e >> 4, c4 = e & 15;
-    *reinterpret_cast<float4*>(&S[r][4 * c4]) =
-        __ldg(reinterpret_cast<const float4*>(base + (long long)r * np + 4 * c4));
-  }
-  if (t < SF) {
-    const float2 a = fs[d.swrow + r0 + t], b = fs[d.swrow + c0 + t];
-    frh[t] = a.x;
-    frl[t] = a.y;
-    fch[t] = b.x;
-    fcl[t] = b.y;
-  }
-  __syncthreads();
-  if (diag) {
-    for (int e = t; e < SF * SF; e += 128) {
-      const int r = e >> 6, cc = e & 63;
-      if (cc < r) S[r][cc] = S[cc][r];
-    }
-    __syncthreads();
-    if (t < SF) S[t][t] = 1.0f;
-    __syncthreads();
-  }
-  const long long ld = (long long)TSn * SF;
-  float2* Pc = P + d.soff;
-  if (accurate && accurate[c] == 0) {
-    if (t < SF) {
-      float acc = 0.f;
-#pragma unroll 4
-      for (int q4 = 0; q4 < SF / 4; ++q4) {
-        const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
-        const float4 fh = *reinterpret_cast<const float4*>(&fch[4 * q4]);
-        acc = fmaf(v.x, fh.x, acc);
-        acc = fmaf(v.y, fh.y, acc);
-        acc = fmaf(v.z, fh.z, acc);
-        acc = fmaf(v.w, fh.w, acc);
+      for (int q = 0; q < SF * SF / 4 / 128; ++q) {
+        const int e = t + 128 * q;
+        const int r = e >> 4, c4 = e & 15;
+        cp_async16(&S[buf][r][4 * c4], base + (long long)r * d.np + 4 * c4);
       }
-      Pc[bj * ld + r0 + t] = make_float2(acc, 0.f);
-    } else if (!diag) {
-      const int q = t - SF;
-      float acc = 0.f;
-#pragma unroll 4
-      for (int r = 0; r < SF; r += 4) {
-        const float4 fh = *reinterpret_cast<const float4*>(&frh[r]);
-        acc = fmaf(S[r][q], fh.x, acc);
-        acc = fmaf(S[r + 1][q], fh.y, acc);
-        acc = fmaf(S[r + 2][q], fh.z, acc);
-        acc = fmaf(S[r + 3][q], fh.w, acc);
+      if (t < SF)
+        cp_async8(&fr[buf][t], fs + d.swrow + bi * SF + t);
+      else
+        cp_async8(&fc[buf][t - SF], fs + d.swrow + bj * SF + (t - SF));
+    }
+    cp_async_commit();
+  };
+  int k = 0;
+  issue(blockIdx.x, 0);
+  for (int id = blockIdx.x; id < total; id += gridDim.x, ++k) {
+    const int buf = k & 1;
+    issue(id + gridDim.x, buf ^ 1);
+    cp_async_wait1();
+    __syncthreads();
+    int c, bi, bj;
+    if (symv_tile(id, tpc, cd, state, c, bi, bj)) {
+      const ChainDesc& d = cd[c];
+      const int TSn = (d.n + SF - 1) / SF;
+      const bool diag = (bi == bj);
+      float (*Sb)[SFP] = S[buf];
+      if (diag) {  // uniform over the CTA
+        for (int e = t; e < SF * SF; e += 128) {
+          const int r = e >> 6, cc = e & 63;
+          if (cc < r) Sb[r][cc] = Sb[cc][r];
+        }
+        __syncthreads();
+        if (t < SF) Sb[t][t] = 1.0f;
+        __syncthreads();
       }
-      Pc[bi * ld + c0 + q] = make_float2(acc, 0.f);
-    }
-    return;
-  }
-  if (t < SF) {
-    DF acc{0.f, 0.f};
+      const int r0 = bi * SF, c0 = bj * SF;
+      const long long ld = (long long)TSn * SF;
+      float2* Pc = P + d.soff;
+      const float4* fc4 = reinterpret_cast<const float4*>(fc[buf]);  // (h0, l0, h1, l1)
+      const float4* fr4 = reinterpret_cast<const float4*>(fr[buf]);
+      const int md = mode ? mode[c] : MOB_FULL_DF;
+      if (md == MOB_FULL_F32 || md == MOB_INC_F32) {
+        if (t < SF) {
+          float acc = 0.f;
 #pragma unroll 4
-    for (int q4 = 0; q4 < SF / 4; ++q4) {
-      const float4 v = *reinterpret_cast<const float4*>(&S[t][4 * q4]);
-      const float4 fh = *reinterpret_cast<const float4*>(&fch[4 * q4]);
-      const float4 fl = *reinterpret_cast<const float4*>(&fcl[4 * q4]);
-      df_add_prod(acc, v.x, fh.x, fl.x);
-      df_add_prod(acc, v.y, fh.y, fl.y);
-      df_add_prod(acc, v.z, fh.z, fl.z);
-      df_add_prod(acc, v.w, fh.w, fl.w);
-    }
-    Pc[bj * ld + r0 + t] = make_float2(acc.hi, acc.lo);  // rows of bi from column block bj
-  } else if (!diag) {
-    const int q = t - SF;
-    DF acc{0.f, 0.f};
+          for (int q4 = 0; q4 < SF / 4; ++q4) {
+            const float4 v = *reinterpret_cast<const float4*>(&Sb[t][4 * q4]);
+            const float4 f01 = fc4[2 * q4], f23 = fc4[2 * q4 + 1];
+            acc = fmaf(v.x, f01.x, acc);
+            acc = fmaf(v.y, f01.z, acc);
+            acc = fmaf(v.z, f23.x, acc);
+            acc = fmaf(v.w, f23.z, acc);
+          }
+          Pc[bj * ld + r0 + t] = make_float2(acc, 0.f);
+        } else if (!diag) {
+          const int q = t - SF;
+          float acc = 0.f;
 #pragma unroll 4
-    for (int r = 0; r < SF; r += 4) {
-      const float4 fh = *reinterpret_cast<const float4*>(&frh[r]);
-      const float4 fl = *reinterpret_cast<const float4*>(&frl[r]);
-      df_add_prod(acc, S[r][q], fh.x, fl.x);
-      df_add_prod(acc, S[r + 1][q], fh.y, fl.y);
-      df_add_prod(acc, S[r + 2][q], fh.z, fl.z);
-      df_add_prod(acc, S[r + 3][q], fh.w, fl.w);
+          for (int r = 0; r < SF; r += 4) {
+            const float4 f01 = fr4[r >> 1], f23 = fr4[(r >> 1) + 1];
+            acc = fmaf(Sb[r][q], f01.x, acc);
+            acc = fmaf(Sb[r + 1][q], f01.z, acc);
+            acc = fmaf(Sb[r + 2][q], f23.x, acc);
+            acc = fmaf(Sb[r + 3][q], f23.z, acc);
+          }
+          Pc[bi * ld + c0 + q] = make_float2(acc, 0.f);
+        }
+      } else {
+        if (t < SF) {
+          DF acc{0.f, 0.f};
+#pragma unroll 4
+          for (int q4 = 0; q4 < SF / 4; ++q4) {
+            const float4 v = *reinterpret_cast<const float4*>(&Sb[t][4 * q4]);
+            const float4 f01 = fc4[2 * q4], f23 = fc4[2 * q4 + 1];
+            df_add_prod(acc, v.x, f01.x, f01.y);
+            df_add_prod(acc, v.y, f01.z, f01.w);
+            df_add_prod(acc, v.z, f23.x, f23.y);
+            df_add_prod(acc, v.w, f23.z, f23.w);
+          }
+          Pc[bj * ld + r0 + t] = make_float2(acc.hi, acc.lo);  // rows of bi from column block bj
+        } else if (!diag) {
+          const int q = t - SF;
+          DF acc{0.f, 0.f};
+#pragma unroll 4
+          for (int r = 0; r < SF; r += 4) {
+            const float4 f01 = fr4[r >> 1], f23 = fr4[(r >> 1) + 1];
+            df_add_prod(acc, Sb[r][q], f01.x, f01.y);
+            df_add_prod(acc, Sb[r + 1][q], f01.z, f01.w);
+            df_add_prod(acc, Sb[r + 2][q], f23.x, f23.y);
+            df_add_prod(acc, Sb[r + 3][q], f23.z, f23.w);
+          }
+          Pc[bi * ld + c0 + q] = make_float2(acc.hi, acc.lo);  // rows of bj from column block bi
+        }
+      }
     }
-    Pc[bi * ld + c0 + q] = make_float2(acc.hi, acc.lo);  // rows of bj from column block bi
+    __syncthreads();  // stage `buf` is refilled by the issue of the next iteration
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 __global__ void k_symv_reduce_df(const ChainDesc* __restrict__ cd, const float2* __restrict__ P,
-                                 double* __restrict__ u, const int* __restrict__ state) {
+                                 double* __restrict__ u, const int* __restrict__ state,
+                                 const int* __restrict__ mode) {
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
@@ -451,25 +506,42 @@ __global__ void k_symv_reduce_df(const ChainDesc* __restrict__ cd, const float2*
     lo += ((hi - (s - bp)) + (v.x - bp)) + v.y;
     hi = s;
   }
-  u[3 * d.boff + row] = (double)hi + (double)lo;
+  const double v = (double)hi + (double)lo;
+  if (mode && mode[c] >= MOB_INC_DF)
+    u[3 * d.boff + row] += v;
+  else
+    u[3 * d.boff + row] = v;
 }
 
 cudaError_t launch_split_f2(const ChainDesc* cd, int n_chains, int max_np, const double* v,
                             float2* out, const int* state, cudaStream_t s) {
-  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, v, out, state);
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, v, nullptr, out, state, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, float2* fsplit, double* scratch, double* u,
-                            const int* state, const int* accurate, cudaStream_t s) {
+                            const double* f, const double* df, float2* fsplit, double* scratch,
+                            double* u, const int* state, const int* mode, cudaStream_t s) {
   const int TSn = ceil_div(max_np, SF);
   float2* P = reinterpret_cast<float2*>(scratch);
-  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, f, fsplit, state);
-  k_symv_tiles_f32<<<dim3(TSn * (TSn + 1) / 2, n_chains), 128, 0, s>>>(M, cd, fsplit, P, state,
-                                                                        accurate);
-  k_symv_reduce_df<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, P, u, state);
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, f, df, fsplit, state, mode);
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
+      n_sm = 1;
+  }
+  const int tpc = TSn * (TSn + 1) / 2;
+  const long long total = (long long)tpc * n_chains;
+  const int grid = (int)(total < (long long)kSymvCtasPerSm * n_sm ? total : (long long)kSymvCtasPerSm * n_sm);
+  k_symv_tiles_f32<<<grid, 128, 0, s>>>(M, cd, n_chains, tpc, fsplit, P, state, mode);
+  k_symv_reduce_df<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, P, u, state, mode);
   return cudaGetLastError();
+}
+
+const void* form_k_kernel(bool fp32) {
+  return fp32 ? (const void*)k_form_k<float> : (const void*)k_form_k<double>;
 }
 
 cudaError_t matvec_configure() {

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
   gmax = block_max(gmax, red);
   if (threadIdx.x == 0) {
     int ns = st;
-    const bool acc_now = !accurate || accurate[c];
+    const bool acc_now = !accurate || accurate[c] != MOB_FULL_F32;
     if (st == NS_EXTRA) {
       ns = NS_DONE;
     } else if (gmax <= ph.tol && acc_now) {
@@ -193,8 +193,18 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
       atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
     }
     state[c] = ns;
-    // the residual decides convergence only when it was evaluated accurately
-    if (accurate && gmax < 1e-5) accurate[c] = 1;
+    // The residual decides convergence only when it was evaluated accurately.
+    // Mobility products: plain FP32 while the residual is large, then one
+    // full double-float product, then increments D (F_new - F_old) of size
+    // ~|g|: double-float while |g| >= 1e-10, plain FP32 below (error ~1e-7
+    // of an increment below 1e-10, far under the tolerance).
+    if (accurate) {
+      const int md = accurate[c];
+      if (md == MOB_FULL_F32)
+        accurate[c] = (gmax < 1e-5) ? MOB_FULL_DF : MOB_FULL_F32;
+      else
+        accurate[c] = (gmax < 1e-10) ? MOB_INC_F32 : MOB_INC_DF;
+    }
   }
 }
 
@@ -344,7 +354,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve_f32(const float*
                                                                   double* __restrict__ Tn,
                                                                   double* __restrict__ F,
                                                                   int* __restrict__ state,
-                                                                  int* __restrict__ iters) {
+                                                                  int* __restrict__ iters,
+                                                                  double* __restrict__ dF) {
   extern __shared__ __align__(16) uint8_t ns_smem[];
   float* zs = reinterpret_cast<float*>(ns_smem);  // [64 nb]: z, then x
   __shared__ __align__(16) float sblk[kS64];
@@ -429,14 +440,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve_f32(const float*
   // T += delta
   for (int k = t; k < m; k += blockDim.x) Tn[d.roff + k] += (double)zs[k];
   __syncthreads();
-  // F(T)
+  // F(T) and F(delta)
   for (int i = t; i < d.N; i += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      double f = 0.0;
-      if (i < m) f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
-      if (i > 0) f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
+      double f = 0.0, g = 0.0;
+      if (i < m) {
+        f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
+        g += (double)zs[i] * uhat[3 * (d.roff + i) + q];
+      }
+      if (i > 0) {
+        f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
+        g -= (double)zs[i - 1] * uhat[3 * (d.roff + i - 1) + q];
+      }
       F[3 * (d.boff + i) + q] = f;
+      if (dF) dF[3 * (d.boff + i) + q] = g;
     }
   }
   if (t == 0) iters[c] += 1;
@@ -451,10 +469,10 @@ constexpr int solve_block() {
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F, int* state,
-                                int* iters, cudaStream_t s) {
+                                int* iters, cudaStream_t s, double* dF) {
   if constexpr (sizeof(T) == 4)
     k_newton_solve_f32<<<n_chains, kSolveThreads, kSolveMaxM * sizeof(float), s>>>(
-        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters);
+        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters, dF);
   else
     k_newton_solve<T, solve_block<T>()><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(
         K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters);
@@ -465,9 +483,11 @@ cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, 
 // loop has run fewer than max_loops times in this step (a chain still active
 // then is failed by k_finalize; with the per-chain cap of max_newton updates
 // the bound is never reached by a correct state machine).
+// count: this instance ends a loop iteration (counted in *loops and in the
+// step's iteration count); otherwise it only decides whether to enter.
 __global__ void k_any_active(const int* __restrict__ state, int n_chains,
                              cudaGraphConditionalHandle h, unsigned long long* loops,
-                             StepArgs* args, int max_loops) {
+                             StepArgs* args, int max_loops, int count) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -475,16 +495,16 @@ __global__ void k_any_active(const int* __restrict__ state, int n_chains,
     if (state[c] == NS_ACTIVE || state[c] == NS_EXTRA) any = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int k = ++args->loops_in_step;
+    const int k = count ? ++args->loops_in_step : args->loops_in_step;
     cudaGraphSetConditional(h, (any && k < max_loops) ? 1u : 0u);
-    *loops += 1;
+    if (count) *loops += 1;
   }
 }
 
 cudaError_t launch_newton_any_active(const int* state, int n_chains, cudaGraphConditionalHandle h,
                                      unsigned long long* loops, StepArgs* args, int max_loops,
-                                     cudaStream_t s) {
-  k_any_active<<<1, 256, 0, s>>>(state, n_chains, h, loops, args, max_loops);
+                                     bool count, cudaStream_t s) {
+  k_any_active<<<1, 256, 0, s>>>(state, n_chains, h, loops, args, max_loops, count ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -596,10 +616,12 @@ cudaError_t launch_set_args(StepArgs* args, const double* noise, long long strid
 
 template cudaError_t launch_newton_solve<double>(const double*, const double*, const ChainDesc*, int,
                                                  Phys, const double*, double*, double*, double*,
-                                                 int*, int*, cudaStream_t);
+                                                 int*, int*, cudaStream_t, double*);
 template cudaError_t launch_newton_solve<float>(const float*, const float*, const ChainDesc*, int,
                                                 Phys, const double*, double*, double*, double*, int*,
-                                                int*, cudaStream_t);
+                                                int*, cudaStream_t, double*);
+
+const void* rod_dirs_kernel() { return (const void*)k_rod_dirs; }
 
 cudaError_t tension_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double, 32>,

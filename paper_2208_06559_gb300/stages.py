@@ -5,7 +5,8 @@
 Creates one context on cuda:0 with seeded random-walk chains, then times each
 stage of the time step through the C ABI with CUDA events on the launching
 stream (assembly, Cholesky factorisation, Brownian displacement, mobility
-product, one full step) and prints one JSON line.  ``--once`` runs every
+product, one full step) and prints one JSON line.  ``--timeline`` prints the
+stage-boundary times of one step launched kernel by kernel (bd_profile_step).  ``--once`` runs every
 stage exactly once without timing (a short, fixed launch sequence for
 kernel profilers).
 """
@@ -34,6 +35,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--once", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated bead counts: time one step per N")
+    ap.add_argument("--timeline", action="store_true",
+                    help="stage-boundary times of one step launched kernel by kernel")
     a = ap.parse_args()
     if a.sweep:
         sweep(a)
@@ -45,6 +48,13 @@ def main():
     ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec)
     ctx.set_state(r0)
     xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 3, int(Nc.sum()), a.seed + 1)).cuda()
+    if a.timeline:
+        ctx.step(xi[0:1])
+        tl = ctx.profile_step(xi[1])
+        tl = ctx.profile_step(xi[2])
+        print(json.dumps({"chains": a.chains, "beads": a.beads, "precision": a.precision,
+                          **{k: round(v, 4) for k, v in tl.items()}}))
+        return
     if a.once:
         ctx.assemble()
         ctx.factor()

@@ -1,5 +1,5 @@
 """Mixed-precision path (FP32 storage, TF32 tensor-core Cholesky updates,
-FP64 diagonal blocks and tension solve) against the FP64 oracle.
+FP32 diagonal tiles, FP64-accurate tension solve) against the FP64 oracle.
 
 Parity here is not bit-level: the factor carries TF32 rounding (10-bit
 mantissa, unit round-off 2^-11 ~ 4.9e-4).  The bounds below follow from that:
@@ -153,3 +153,30 @@ def test_factor_tuning_and_configs(bd, tmp_path):
     obs, st = ctx.observables()
     assert (st == 0).all() and obs[:, 6].max().item() < 1e-10
     ctx.close()
+
+
+def test_profiled_step_equals_graph_step(bd):
+    """bd_profile_step launches the step's kernels one by one (no graph) with
+    stage events: the state after it equals the state after bd_step bit for
+    bit, and the stage times are positive and add up to the step."""
+    Nc = np.array([300, 1000, 86], np.int32)
+    r0 = inputs.random_walk(Nc, 31)
+    noise = cuda(inputs.gaussian_noise(1, int(Nc.sum()), 32))
+    out = []
+    for prof in (False, True):
+        ctx = bd.Context(Nc, precision=bd.MIXED_TF32, flow=1, Wi=100.0)
+        ctx.set_state(cuda(r0))
+        if prof:
+            tl = ctx.profile_step(noise[0])
+            assert set(tl) == set(bd.Context.PROFILE_STAGES)
+            assert all(v > 0 for v in tl.values())
+            parts = sum(tl[k] for k in ("assemble", "factor", "brownian", "k_wait_predictor", "tension",
+                                        "commit"))
+            assert abs(parts - tl["step"]) <= 1e-3 * tl["step"] + 1e-3
+        else:
+            ctx.step(noise)
+        st, _ = ctx.chain_status()
+        assert (st == 0).all()
+        out.append(ctx.get_state().cpu().numpy())
+        ctx.close()
+    np.testing.assert_array_equal(out[0], out[1])
