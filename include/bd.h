@@ -11,7 +11,11 @@
  *   4. add the flow drift dt kappa.r (Eq. (5)/(6)) and the tension drift
  *      dt D F(T) (constraint-force term of Eq. (6));
  *   5. solve for the rod tensions T that keep every rod at unit length (the
- *      rigid, K* -> infinity limit of the semi-implicit scheme of Eqs. (13)-(17)).
+ *      rigid, K* -> infinity limit of the semi-implicit scheme of Eqs. (13)-(17)),
+ *      or, with BD_FRAENKEL, the paper's own finite-K* semi-implicit update of
+ *      Fraenkel springs (Sec. 3 Eq. (3), eqQ2, Eqs. (23)-(25)): steps 1-3, one
+ *      mobility product with the spring forces at t, then a closed-form
+ *      update per link.
  *
  * Conventions.  A chain has N >= 2 beads and N-1 rods; rod k joins bead k to
  * bead k+1.  Rod length b = 1 and bead mobility kT/zeta = 1, so D_ii = I.
@@ -62,7 +66,7 @@ typedef enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2 } bd_fl
  * operands, FP32 accumulation), FP64 diagonal-block factorisation, one
  * refinement step on the Brownian displacement, FP64 tension solve. */
 typedef enum { BD_FP64 = 0, BD_MIXED_TF32 = 1, BD_MIXED_BF16 = 2 } bd_precision;
-typedef enum { BD_RIGID = 0 } bd_constraint;
+typedef enum { BD_RIGID = 0, BD_FRAENKEL = 1 } bd_constraint;
 
 /* Observables written per chain by bd_observables (Sec. 5 Eqs. (25)-(29)). */
 #define BD_OBS_STRIDE 12
@@ -91,14 +95,16 @@ typedef struct {
   double Wi;             /* Weissenberg number; rate = Wi / lambda */
   double lambda;         /* relaxation time; <= 0 means 1 */
   int precision;         /* bd_precision */
-  int constraint;        /* bd_constraint (BD_RIGID) */
+  int constraint;        /* bd_constraint: BD_RIGID (tension solve) or BD_FRAENKEL */
   double tol;            /* Newton tolerance on max_k | |Q_k|^2 - 1 |; <= 0 -> 1e-13 */
   int max_newton;        /* Newton update cap; <= 0 -> 50 */
   int refine;            /* mixed precision: 1 = one refinement step on B xi */
+  double k_spring;       /* BD_FRAENKEL: spring constant K* > 0 (Eq. (3)); unused for BD_RIGID */
 } bd_params;
 
 /* Fill *p with defaults: 1 chain (n_beads NULL), h* = 0.25, a = h*, dt = 1e-4,
- * no flow, lambda = 1, BD_FP64, tol 1e-13, max_newton 50, refine 1. */
+ * no flow, lambda = 1, BD_FP64, BD_RIGID, tol 1e-13, max_newton 50, refine 1,
+ * k_spring 1e4. */
 void bd_params_default(bd_params* p);
 
 /* Create a context on the current CUDA device: validates *p, copies n_beads,

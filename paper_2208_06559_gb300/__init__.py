@@ -4,8 +4,8 @@ dynamics with hydrodynamic interaction (arXiv 2208.06559).
 The compute lives in libbd.so (CUDA kernels behind the C ABI of include/bd.h);
 ``binding`` marshals torch tensors into it and ``build`` compiles it.
 """
-from .binding import (FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL, FP64, MIXED_BF16, MIXED_TF32,
-                      OBS_STRIDE, BDError, Context, lib)
+from .binding import (FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL, FP64, FRAENKEL, MIXED_BF16, MIXED_TF32,
+                      OBS_STRIDE, RIGID, BDError, Context, lib)
 
 __all__ = ["Context", "BDError", "lib", "FLOW_NONE", "FLOW_SHEAR", "FLOW_UNIAXIAL", "FP64",
-           "MIXED_TF32", "MIXED_BF16", "OBS_STRIDE"]
+           "MIXED_TF32", "MIXED_BF16", "OBS_STRIDE", "RIGID", "FRAENKEL"]

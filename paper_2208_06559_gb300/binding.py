@@ -27,6 +27,7 @@ BD_ERR_STATE = -7
 
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+RIGID, FRAENKEL = 0, 1
 OBS_STRIDE = 12
 # column indices of the observables row (include/bd.h BD_OBS_*)
 OBS_REE_X, OBS_R2, OBS_RG2, OBS_STRETCH, OBS_MAXDEV, OBS_NEWTON = 0, 3, 4, 5, 6, 7
@@ -50,6 +51,7 @@ class Params(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("max_newton", ctypes.c_int),
         ("refine", ctypes.c_int),
+        ("k_spring", ctypes.c_double),
     ]
 
 
@@ -156,7 +158,7 @@ class Context:
     def __init__(self, n_beads: Sequence[int], h_star: float = 0.25, dt: float = 1e-4,
                  flow: int = FLOW_NONE, Wi: float = 0.0, lam: float = 1.0, a: float = 0.0,
                  precision: int = FP64, tol: float = 1e-13, max_newton: int = 50,
-                 refine: int = 1):
+                 refine: int = 1, constraint: int = RIGID, k_spring: float = 1e4):
         L = lib()
         self.n_beads = np.ascontiguousarray(np.asarray(n_beads, dtype=np.int32))
         self.n_chains = int(self.n_beads.shape[0])
@@ -169,10 +171,12 @@ class Context:
         p.h_star, p.a, p.dt = float(h_star), float(a), float(dt)
         p.flow, p.Wi, p.lambda_ = int(flow), float(Wi), float(lam)
         p.precision, p.tol, p.max_newton, p.refine = int(precision), float(tol), int(max_newton), int(refine)
+        p.constraint, p.k_spring = int(constraint), float(k_spring)
         h = ctypes.c_void_p()
         _check(L.bd_create(ctypes.byref(p), ctypes.byref(h)), "bd_create")
         self._h = h
         self.precision = int(precision)
+        self.constraint = int(constraint)
 
     def close(self):
         if getattr(self, "_h", None):

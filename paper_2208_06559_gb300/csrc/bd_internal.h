@@ -46,6 +46,7 @@ struct Phys {
   double tol;
   int max_newton;
   int n_chains;
+  double kspring;  // Fraenkel spring constant K* (Fraenkel mode)
 };
 
 // Device-side step arguments (read by the captured step graph each replay).
@@ -138,6 +139,13 @@ cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_ch
 cudaError_t matvec_configure();
 cudaError_t assemble_configure();
 cudaError_t tension_configure();
+// Fraenkel-spring mode (k_fraenkel.cu).
+cudaError_t launch_fraenkel_forces(const double* r, const ChainDesc* cd, int n_chains, int max_N,
+                                   double kspring, double* F, cudaStream_t s);
+cudaError_t launch_fraenkel_update(double* r, const double* y, const double* u, const ChainDesc* cd,
+                                   int n_chains, Phys ph, double* T, const int* status, int* iters,
+                                   cudaStream_t s);
+cudaError_t launch_step_done(StepArgs* args, cudaStream_t s);
 // Kernels of the rod-coupling-matrix chain (K formation and factorisation),
 // for per-node priorities in the captured step graph.
 const void* form_k_kernel(bool fp32);

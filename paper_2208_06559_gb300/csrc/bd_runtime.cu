@@ -81,6 +81,7 @@ struct bd_ctx {
   int graph_unroll = 0;  // tension iterations captured as plain graph nodes before the WHILE node
   int while_cap = 1;     // WHILE-node iterations allowed per step
   cudaEvent_t* prof = nullptr;  // bd_profile_step: stage-boundary events
+  bool fraenkel = false;        // BD_FRAENKEL: semi-implicit spring update instead of the tension solve
   std::mutex mu;
 };
 
@@ -279,8 +280,48 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
   cudaGetLastError();
 }
 
+// Fraenkel-spring step (Sec. 3): D, its factor and the Brownian displacement
+// as for rigid rods, the bead forces of the springs, one mobility product,
+// then the per-link semi-implicit update, which also commits the positions.
+int enqueue_step_fraenkel(bd_ctx* c, cudaStream_t s) {
+  int rc;
+  prof_mark(c, 0, s);
+  if ((rc = enqueue_assemble(c, s))) return rc;
+  prof_mark(c, 1, s);
+  prof_mark(c, 7, s);  // no K chain in this mode
+  if ((rc = enqueue_factor(c, s))) return rc;
+  prof_mark(c, 2, s);
+  if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
+  prof_mark(c, 3, s);
+  CK(launch_fraenkel_forces(c->r, c->d_cd, c->n_chains, c->max_N, c->ph.kspring, c->F, s));
+  if ((rc = enqueue_symv(c, c->F, c->u, nullptr, s))) return rc;
+  prof_mark(c, 4, s);
+  CK(launch_fraenkel_update(c->r, c->y, c->u, c->d_cd, c->n_chains, c->ph, c->T, c->status, c->iters, s));
+  prof_mark(c, 5, s);
+  CK(launch_step_done(c->args, s));
+  prof_mark(c, 6, s);
+  return BD_OK;
+}
+
 int build_step_graph(bd_ctx* c) {
   if (c->exec) return BD_OK;
+  if (c->fraenkel) {
+    cudaStream_t s = c->cs;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step_fraenkel(c, s);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(s, &g));
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    set_graph_priorities(c, g);
+    c->graph = g;
+    c->graph_kernels = count_kernel_nodes(g);
+    c->body_kernels = 0;
+    CK(cudaGraphInstantiate(&c->exec, g, cudaGraphInstantiateFlagUseNodePriority));
+    return BD_OK;
+  }
   cudaStream_t s = c->cs;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = enqueue_pre_newton(c, s);
@@ -345,6 +386,7 @@ int build_step_graph(bd_ctx* c) {
 // graph's conditional node: the same kernels, with the tension-solve body
 // enqueued a fixed number of times (converged chains skip it on the device).
 int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
+  if (c->fraenkel) return enqueue_step_fraenkel(c, s);
   int rc;
   prof_mark(c, 0, s);
   if ((rc = enqueue_pre_newton(c, s))) return rc;
@@ -457,6 +499,7 @@ void bd_params_default(bd_params* p) {
   p->tol = 1e-13;
   p->max_newton = 50;
   p->refine = 1;
+  p->k_spring = 1e4;
 }
 
 const char* bd_strerror(int code) {
@@ -507,7 +550,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (p->h_star > 0.0 && a < p->h_star) return BD_ERR_ARG;  // D may not be positive definite
   if (p->flow < BD_FLOW_NONE || p->flow > BD_FLOW_UNIAXIAL) return BD_ERR_ARG;
   if (p->precision < BD_FP64 || p->precision > BD_MIXED_BF16) return BD_ERR_ARG;
-  if (p->constraint != BD_RIGID) return BD_ERR_ARG;
+  if (p->constraint != BD_RIGID && p->constraint != BD_FRAENKEL) return BD_ERR_ARG;
+  if (p->constraint == BD_FRAENKEL && !(p->k_spring > 0.0 && p->k_spring < 1e300)) return BD_ERR_ARG;
   // limits of the per-chain kernels: the tension solve holds N - 1 <= 4096
   // unknowns in shared memory; the refinement's triangular solve owns up to
   // 12 columns per thread of a 1024-thread block (3N <= 12288 after padding)
@@ -542,6 +586,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   ph.tol = p->tol > 0.0 ? p->tol : 1e-13;
   ph.max_newton = p->max_newton > 0 ? p->max_newton : 50;
   ph.n_chains = c->n_chains;
+  ph.kspring = p->constraint == BD_FRAENKEL ? p->k_spring : 0.0;
+  c->fraenkel = p->constraint == BD_FRAENKEL;
   if (const char* e = getenv("BD_STEP_DIRECT")) {
     const int v = atoi(e);
     c->direct_iters = v > 0 ? (v == 1 ? ph.max_newton + 2 : v) : 0;
@@ -860,7 +906,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
                const double* dJdr_final_dev, double grad_host[2], void* stream) {
   (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
   if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
-  if (c->mixed || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
+  if (c->mixed || c->fraenkel || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
