@@ -115,7 +115,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     prec = {"fp64": bd.FP64, "tf32": bd.MIXED_TF32}[args.precision] if args.precision else \
         (bd.MIXED_TF32 if w.precision != 0 else bd.FP64)
-    kw = dict(h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol)
+    kw = dict(h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol, constraint=w.constraint,
+              k_spring=w.kspring)
 
     def barrier():
         if world > 1:
@@ -260,6 +261,8 @@ def run_ours(args, rank, world, local_rank):
                        "hstar": w.hstar, "a": w.hstar, "dt": w.dt,
                        "flow": ["none", "shear", "uniaxial"][w.flow], "Wi": w.Wi, "lambda": 1.0,
                        "newton_tol": args.tol,
+                       "constraint": ["rigid", "fraenkel"][w.constraint],
+                       **({"k_spring": w.kspring} if w.constraint == 1 else {}),
                        "precision": "fp64" if prec == bd.FP64 else "mixed_tf32_refined",
                        "l2": f"inputs larger than L2 (per-step matrices {mat_gb:.1f} GB)",
                        "parallelism": f"independent replicas x{world}"},
@@ -276,7 +279,8 @@ def cpu_baseline(w, Nc, r0, noise_host, max_chains):
     import oracle as orc
     cores = orc.num_threads()
     S = int(min(len(Nc), max(1, min(cores, max_chains))))
-    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi)
+    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, constraint=w.constraint,
+                        kspring=w.kspring)
     Ns = Nc[:S]
     rs = r0[: int(Ns.sum())]
     nz = np.ascontiguousarray(noise_host[:1, : int(Ns.sum())])
@@ -298,7 +302,8 @@ def run_reference(args, rank, world):
     Ns = Nc[:S]
     r = inputs.random_walk(Ns, w.seed)
     noise = inputs.gaussian_noise(args.steps + args.warmup, int(Ns.sum()), w.seed + 1)
-    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol)
+    p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol,
+                        constraint=w.constraint, kspring=w.kspring)
     for i in range(args.warmup):
         r, *_ = orc.run(p, Ns, r, noise[i:i + 1])
     t0 = time.perf_counter()

@@ -74,6 +74,8 @@ class Workload:
     precision: int          # 0 fp64, 1 mixed tf32, 2 mixed bf16
     seed: int
     uneven: tuple = ()      # (lo, hi) for drawn lengths
+    constraint: int = 0     # 0 rigid rods (tension solve), 1 Fraenkel springs
+    kspring: float = 1e4    # Fraenkel spring constant K*
 
     def lengths(self) -> np.ndarray:
         if self.uneven:
@@ -81,7 +83,8 @@ class Workload:
         return np.full(self.n_chains, self.n_beads, dtype=np.int32)
 
 
-# The five workloads of the build's measurement plan (seed = 1234 + id).
+# The workloads of the measurement plan (seed = 1234 + id): five rigid-rod
+# workloads and one with the paper's Fraenkel springs.
 WORKLOADS = {
     "n16_fp64_eq": Workload("n16_fp64_eq", 1, 16, 0.25, 1e-4, 0, 0.0, 1000, 0, 1235),
     "n100x256_fp64_uniaxial": Workload("n100x256_fp64_uniaxial", 256, 100, 0.25, 1e-4, 2,
@@ -92,4 +95,7 @@ WORKLOADS = {
                                        50.0, 100, 1, 1238),
     "uneven50to500x128_fp64": Workload("uneven50to500x128_fp64", 128, 0, 0.25, 1e-4, 2,
                                        5.0, 200, 0, 1239, (50, 500)),
+    # the paper's own constraint mode (Fraenkel springs, K* = 1e4 at dt = 1e-4)
+    "n1000x64_mixed_fraenkel_shear": Workload("n1000x64_mixed_fraenkel_shear", 64, 1000, 0.25, 1e-4,
+                                              1, 100.0, 500, 1, 1240, (), 1, 1e4),
 }
