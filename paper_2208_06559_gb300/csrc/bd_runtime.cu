@@ -69,7 +69,7 @@ struct bd_ctx {
   cudaEvent_t gev[kMaxGroups + 1] = {};
   // concurrent branches of the step: the K chain, the refinement's solve
   cudaStream_t aux[2] = {};
-  cudaEvent_t aev[4] = {};
+  cudaEvent_t aev[6] = {};  // [0,1] K-chain fork/join, [2,3] refinement fork/join, [4,5] caller-stream fence
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // forward-mode tangent workspace (allocated by the first bd_adjoint call)
@@ -534,7 +534,7 @@ void bd_destroy(bd_ctx* c) {
     if (c->gev[g]) cudaEventDestroy(c->gev[g]);
   for (int g = 0; g < 2; ++g)
     if (c->aux[g]) cudaStreamDestroy(c->aux[g]);
-  for (int g = 0; g < 4; ++g)
+  for (int g = 0; g < 6; ++g)
     if (c->aev[g]) cudaEventDestroy(c->aev[g]);
   if (c->cs) cudaStreamDestroy(c->cs);
   if (c->cs2) cudaStreamDestroy(c->cs2);
@@ -691,7 +691,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       cudaStreamCreateWithPriority(&c->aux[0], cudaStreamNonBlocking, pr_low) != cudaSuccess ||
       cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, pr_high) != cudaSuccess)
     return fail(BD_ERR_CUDA);
-  for (int g = 0; g < 4; ++g)
+  for (int g = 0; g < 6; ++g)
     if (cudaEventCreateWithFlags(&c->aev[g], cudaEventDisableTiming) != cudaSuccess)
       return fail(BD_ERR_CUDA);
   cudaStream_t s = c->cs;
@@ -778,13 +778,22 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
     nz = c->stage;
   }
   CK(launch_set_args(c->args, nz, stride, s));
+  // The steps run on the context's highest-priority stream, ordered after the
+  // caller's work on `stream` and before the caller's later work on it (a
+  // default-priority caller stream would share the lowest priority with the
+  // K chain and lose the factorisation's precedence over it).
+  cudaStream_t cs = c->cs;
+  CK(cudaEventRecord(c->aev[4], s));
+  CK(cudaStreamWaitEvent(cs, c->aev[4], 0));
   if (c->direct_iters > 0) {
     for (int i = 0; i < n_steps; ++i)
-      if ((rc = enqueue_step_direct(c, s))) return rc;
-    return BD_OK;
+      if ((rc = enqueue_step_direct(c, cs))) return rc;
+  } else {
+    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, cs));
+    c->steps_launched += (unsigned long long)n_steps;
   }
-  for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, s));
-  c->steps_launched += (unsigned long long)n_steps;
+  CK(cudaEventRecord(c->aev[5], cs));
+  CK(cudaStreamWaitEvent(s, c->aev[5], 0));
   return BD_OK;
 }
 

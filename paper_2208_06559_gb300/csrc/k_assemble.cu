@@ -9,6 +9,8 @@
 // at (j, i).  The result is the full symmetric D in the chain's row-major
 // matrix; the Cholesky later overwrites the lower triangle with the factor and
 // the strict upper triangle keeps D.
+#include <type_traits>
+
 #include "bd_internal.h"
 
 namespace bd {
@@ -103,21 +105,37 @@ __global__ void __launch_bounds__(256) k_assemble(const double* __restrict__ r, 
   }
   __syncthreads();
 
+  // 16-byte row stores (4 floats or 2 doubles); rows and columns past the
+  // logical order n are never written (the padded border keeps its identity
+  // diagonal, and a tile may reach past the padded order of the FP64 layout)
   T* base = M + d.moff;
   const long long np = d.np;
+  const int n = d.n;
   const int r0 = kElTile * bi, c0 = kElTile * bj;
-  for (int e = threadIdx.x; e < kElTile * kElTile; e += blockDim.x) {
-    const int rr = e / kElTile, cc = e % kElTile;
-    const int row = r0 + rr, col = c0 + cc;
-    if (row < d.n && col < d.n) base[row * np + col] = S[rr][cc];
-  }
-  if (bi != bj) {
-    for (int e = threadIdx.x; e < kElTile * kElTile; e += blockDim.x) {
-      const int rr = e / kElTile, cc = e % kElTile;
-      const int row = c0 + rr, col = r0 + cc;
-      if (row < d.n && col < d.n) base[row * np + col] = S[cc][rr];
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int G = kElTile / V;  // vectors per tile row
+  using VecT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  auto store_rows = [&](int rbase, int cbase, bool transposed) {
+    for (int e = threadIdx.x; e < kElTile * G; e += blockDim.x) {
+      const int rr = e / G, g = e - rr * G;
+      const int row = rbase + rr, col = cbase + V * g;
+      if (row >= n || col >= n) continue;
+      VecT vv;
+      T* vp = reinterpret_cast<T*>(&vv);
+#pragma unroll
+      for (int q = 0; q < V; ++q) vp[q] = transposed ? S[V * g + q][rr] : S[rr][V * g + q];
+      T* dst = base + (long long)row * np + col;
+      if (col + V <= n) {
+        *reinterpret_cast<VecT*>(dst) = vv;
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+          if (col + q < n) dst[q] = vp[q];
+      }
     }
-  }
+  };
+  store_rows(r0, c0, false);
+  if (bi != bj) store_rows(c0, r0, true);
 }
 
 template <typename T>

@@ -13,6 +13,8 @@
 // (double-float): each xi or z value is split into two floats, each product
 // d * hi is made exact with an FMA and summed with two-sum, so the results
 // carry FP64-level accuracy without FP64 arithmetic (slow on this part).
+#include <cooperative_groups.h>
+
 #include "bd_internal.h"
 
 namespace bd {
@@ -193,6 +195,127 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __rest
   }
 }
 
+// The same solve split over a cluster of two CTAs per chain: CTA `rank` owns
+// the columns of the 128-wide blocks B with B % 2 == rank (local column
+// l = t + 1024 q -> block 2 (l / 128) + rank).  For block b the owner
+// publishes its 128 accumulated sums through distributed shared memory,
+// both CTAs form z_b (the same arithmetic, so identical copies), and each
+// adds block b's contributions to the columns it owns.  Rank 0 writes z.
+constexpr int kTrsvColsCl = 6;  // owned columns per thread: np <= 12288
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
+    k_trsv_t_f32c(const float* __restrict__ M, const float* __restrict__ Winv, const ChainDesc* __restrict__ cd,
+                  const double* __restrict__ x_in, const StepArgs* __restrict__ args, double* __restrict__ z) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) float tv_smem[];
+  float* Ws = tv_smem;                       // [128][128] W_bb
+  float* ph = Ws + kMixedTile * kMixedTile;  // [8][128] partial hi
+  float* pl = ph + 8 * kMixedTile;           // [8][128] partial lo
+  __shared__ float pub_h[2][128], pub_l[2][128];  // published sums of an owned block (by parity)
+  __shared__ float zh[128], zl[128], sh[128], sl[128];
+  const ChainDesc d = cd[blockIdx.x >> 1];
+  const int T = d.np / kMixedTile;
+  const double* x = args ? args->noise + (long long)args->step * args->stride : x_in;
+  x += 3 * d.boff;
+  const float* base = M + d.moff;
+  const long long np = d.np;
+  const int t = threadIdx.x;
+  DFa acc[kTrsvColsCl];
+#pragma unroll
+  for (int q = 0; q < kTrsvColsCl; ++q) acc[q] = DFa{0.f, 0.f};
+  auto col_of = [&](int q) {  // global column of owned slot q (may be >= np)
+    const int l = t + kTrsvThreads * q;
+    return kMixedTile * (2 * (l >> 7) + rank) + (l & 127);
+  };
+  int par = 0;
+  for (int b = T - 1; b >= 0; --b, par ^= 1) {
+    const int c0 = 128 * b;
+    {  // stage W_bb
+      const float4* Wg = reinterpret_cast<const float4*>(Winv + ((long long)d.wrow + c0) * kMixedTile);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(Ws)[t + kTrsvThreads * q] = __ldg(Wg + t + kTrsvThreads * q);
+    }
+    if ((b & 1) == rank) {  // publish the sums of block b's columns
+#pragma unroll
+      for (int q = 0; q < kTrsvColsCl; ++q) {
+        const int a = col_of(q);
+        if (a >= c0 && a < c0 + 128) {
+          pub_h[par][a - c0] = acc[q].hi;
+          pub_l[par][a - c0] = acc[q].lo;
+        }
+      }
+    }
+    cl.sync();
+    if (t < 128) {
+      const int owner = b & 1;
+      const float* qh = owner == rank ? pub_h[par] : cl.map_shared_rank(&pub_h[par][0], owner);
+      const float* ql = owner == rank ? pub_l[par] : cl.map_shared_rank(&pub_l[par][0], owner);
+      const int a = c0 + t;
+      const double rhs = ((a < d.n) ? x[a] : 0.0) - ((double)qh[t] + (double)ql[t]);
+      sh[t] = (float)rhs;
+      sl[t] = (float)(rhs - (double)sh[t]);
+    }
+    __syncthreads();
+    {  // z_i = sum_{j >= i} W[j][i] s_j: output i = t % 128, rows j in [16 p, 16 p + 16)
+      const int i = t & 127, p = t >> 7;
+      DFa zi{0.f, 0.f};
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = 16 * p + jj;
+        if (j >= i) dfa_add_prod(zi, Ws[j * kMixedTile + i], sh[j], sl[j]);
+      }
+      ph[p * kMixedTile + i] = zi.hi;
+      pl[p * kMixedTile + i] = zi.lo;
+    }
+    __syncthreads();
+    if (t < 128) {
+      DFa zi{ph[t], pl[t]};
+#pragma unroll
+      for (int p = 1; p < 8; ++p) dfa_add(zi, ph[p * kMixedTile + t], pl[p * kMixedTile + t]);
+      const double v = (double)zi.hi + (double)zi.lo;
+      zh[t] = (float)v;
+      zl[t] = (float)(v - (double)zh[t]);
+      if (rank == 0 && c0 + t < d.n) z[3 * d.boff + c0 + t] = v;
+    }
+    __syncthreads();
+    if (b > 0) {  // contributions of block b to the owned columns a < c0
+#pragma unroll
+      for (int q = 0; q < kTrsvColsCl; ++q) {
+        const int a = col_of(q);
+        if (a < c0) {
+          // next 16 rows loaded while the current 16 are summed, into two
+          // independent accumulators (even and odd rows)
+          const float* col = base + (long long)c0 * np + a;
+          DFa s0 = acc[q], s1{0.f, 0.f};
+          float v[16], vn[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) v[jj] = __ldg(col + (long long)jj * np);
+#pragma unroll 1
+          for (int r0 = 0; r0 < 128; r0 += 16) {
+            if (r0 + 16 < 128) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) vn[jj] = __ldg(col + (long long)(r0 + 16 + jj) * np);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; jj += 2) {
+              dfa_add_prod(s0, v[jj], zh[r0 + jj], zl[r0 + jj]);
+              dfa_add_prod(s1, v[jj + 1], zh[r0 + jj + 1], zl[r0 + jj + 1]);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = vn[jj];
+          }
+          dfa_add(s0, s1.hi, s1.lo);
+          acc[q] = s0;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();  // no CTA leaves while its partner may still read its shared memory
+}
+
 // y = scale / 2 (y1 + w)   (scale already applied to y1 when y1 was formed
 // with `scale`; here both y1 and w are unscaled).
 __global__ void k_refine_combine(const ChainDesc* __restrict__ cd, const double* __restrict__ y1,
@@ -219,7 +342,7 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
   cudaError_t e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
   if (e != cudaSuccess) return e;
-  k_trsv_t_f32<<<n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
+  k_trsv_t_f32c<<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
   k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
   e = cudaEventRecord(ev[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
@@ -231,7 +354,10 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
 }
 
 cudaError_t refine_configure() {
-  return cudaFuncSetAttribute(k_trsv_t_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_trsv_t_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_trsv_t_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  return e;
 }
 
 }  // namespace bd
