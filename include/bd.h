@@ -148,8 +148,9 @@ int bd_chain_status(bd_ctx* ctx, int* status_host, int* newton_host, void* strea
  * factorisation, Brownian displacement, wait for the rod-coupling matrix K
  * (built on a second stream) plus the predictor, tension iterations,
  * commit, whole step, and the end of the K chain measured from the start of
- * the step.  The state advances by one step as with bd_step.  Synchronises
- * the context's stream.  Errors: BD_ERR_ARG (NULL or host noise),
+ * the step.  The state advances by one step as with bd_step.  It runs on the
+ * context's own stream, where bd_step runs too; work the caller enqueued on
+ * other streams must be complete.  Synchronises the context's stream.  Errors: BD_ERR_ARG (NULL or host noise),
  * BD_ERR_STATE (no state), BD_ERR_CUDA. */
 int bd_profile_step(bd_ctx* ctx, const double* noise, int newton_iters, double* ms_out);
 

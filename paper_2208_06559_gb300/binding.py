@@ -246,7 +246,9 @@ class Context:
     def profile_step(self, noise, newton_iters: int = 0) -> dict:
         """One step launched kernel by kernel with stage-boundary events:
         {stage: ms}, keys PROFILE_STAGES (k_chain_end from the step start)."""
+        import torch
         assert noise.is_cuda and noise.is_contiguous()
+        torch.cuda.synchronize()  # earlier work on other streams (e.g. set_state) is finished
         out = (ctypes.c_double * 8)()
         _check(lib().bd_profile_step(self._h, _ptr(noise), int(newton_iters), out), "bd_profile_step")
         return dict(zip(self.PROFILE_STAGES, list(out)))
