@@ -200,8 +200,9 @@ int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noi
  * The tensor-core factorisation has two shape parameters: the super-panel
  * width (tile columns whose trailing update is applied together, K = 128 x
  * panel) and the number of chain groups factored concurrently on separate
- * streams.  bd_tune_factor times every combination of panel {1, 2, 4, 8} and
- * groups {1, 2, 4, 8} (groups <= chains) on the context's current positions,
+ * streams.  bd_tune_factor times every combination of panel {2, 4, 6, 8, 12}
+ * and groups {1, 2, 4, 8, 12, 16} (groups <= chains) on the context's current
+ * positions,
  * keeps the fastest and reports it (any output pointer may be NULL);
  * bd_set_factor_config applies a known choice (e.g. from a cache).  Both drop
  * the captured step graph, which is rebuilt by the next bd_step.  Mixed

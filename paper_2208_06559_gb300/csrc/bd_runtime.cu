@@ -60,7 +60,7 @@ struct bd_ctx {
   int pr_high = 0, pr_low = 0;  // highest (numerically lowest) and lowest stream priorities
   // mixed factorisation: chain groups on their own streams, so that one
   // group's latency-bound diagonal-tile step overlaps another's products
-  static constexpr int kMaxGroups = 8;
+  static constexpr int kMaxGroups = 16;
   int n_groups = 1;
   int panel = 4;                     // super-panel width of the mixed factorisation (tiles)
   std::vector<int> group_start;      // chain index of each group's first chain (+ end)
@@ -1042,14 +1042,14 @@ int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, v
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int panels[] = {1, 2, 4, 8};
-  const int groups[] = {1, 2, 4, 8};
+  const int panels[] = {2, 4, 6, 8, 12};
+  const int groups[] = {1, 2, 4, 8, 12, 16};
   double best = 1e30;
   int bp = c->panel, bg = c->n_groups;
   int rc = BD_OK;
-  for (int gi = 0; gi < 4 && rc == BD_OK; ++gi) {
+  for (int gi = 0; gi < 6 && rc == BD_OK; ++gi) {
     if (groups[gi] > c->n_chains) continue;
-    for (int pi = 0; pi < 4 && rc == BD_OK; ++pi) {
+    for (int pi = 0; pi < 5 && rc == BD_OK; ++pi) {
       c->panel = panels[pi];
       set_groups(c, groups[gi]);
       float tot = 0.f;
