@@ -88,16 +88,19 @@ template <typename T>
 cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_np,
                         const double* f, double* scratch, double* u, const int* state,
                         cudaStream_t s);
-// Per-chain mode of the FP32-storage mobility product inside the tension
-// iteration (k_matvec.cu): the full product u = D f or the increment
-// u += D df, in plain FP32 or in compensated (double-float) FP32.
+// Per-chain mode of the mixed path's rod-space product inside the tension
+// iteration (k_gmode.cu): the full product w = G T or the increment
+// w += G dT, in plain FP32 or in compensated (double-float) FP32.
 enum MobMode : int { MOB_FULL_F32 = 0, MOB_FULL_DF = 1, MOB_INC_DF = 2, MOB_INC_F32 = 3 };
-// FP32-storage mobility product.  fsplit: [sum np] float2; scratch: the
-// two-phase partials; mode: per chain (NULL = full product, double-float;
-// df unused then).
+// FP32-storage mobility product u = D f to FP64-level accuracy (double-float
+// sums).  fsplit: [sum np] float2; scratch: the two-phase partials.
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, const double* df, float2* fsplit, double* scratch,
-                            double* u, const int* state, const int* mode, cudaStream_t s);
+                            const double* f, float2* fsplit, double* scratch, double* u,
+                            const int* state, cudaStream_t s);
+// Mixed path: K (FP32) and optionally G = C D C^T U (three planes [3][mp][mp]
+// per chain at 3 koff) from the positions, without D (k_matvec.cu).
+cudaError_t launch_form_k_pos(const double* r, float* K, float* G, const ChainDesc* cd, int n_chains,
+                              int max_m, const double* u, double hstar, double a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s);
@@ -108,17 +111,26 @@ cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* 
                              int n_chains, int max_N, Phys ph, double* rstar,
                              const double* uhat, double* T, double* F, int* state,
                              const int* status, int* iters, int* accurate, cudaStream_t s);
-// `accurate` (may be NULL): per chain, set to 1 once max|g| < 1e-5 (the
-// next mobility product must then be FP64-accurate).
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs,
-                                   int* state, int* status, const int* iters, int* accurate,
-                                   cudaStream_t s);
-// dF (optional): F(delta), the change of the forces, for incremental products.
+                                   int* state, int* status, const int* iters, cudaStream_t s);
+// dT (optional, FP32 factor only): the update itself, per rod -- for the
+// incremental rod-space products.
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F,
-                                int* state, int* iters, cudaStream_t s, double* dF = nullptr);
+                                int* state, int* iters, cudaStream_t s, double* dT = nullptr);
+// Rod-space tension iteration of the mixed path (k_gmode.cu).
+cudaError_t launch_tension_products_g(const float* G, const ChainDesc* cd, int n_chains, int max_mp,
+                                      const double* T, const double* dT, double* w, const int* state,
+                                      const int* mode, cudaStream_t s);
+cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const ChainDesc* cd,
+                                     int n_chains, Phys ph, double* rhs, int* state, int* status,
+                                     const int* iters, int* mode, cudaStream_t s);
+cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const double* rstar,
+                              const double* w, const double* F, double* r, const int* state, int* status,
+                              StepArgs* args, cudaStream_t s);
+cudaError_t gmode_configure();
 cudaError_t launch_newton_any_active(const int* state, int n_chains,
                                      cudaGraphConditionalHandle h, unsigned long long* loops,
                                      StepArgs* args, int max_loops, bool count, cudaStream_t s);
@@ -149,6 +161,7 @@ cudaError_t launch_step_done(StepArgs* args, cudaStream_t s);
 // Kernels of the rod-coupling-matrix chain (K formation and factorisation),
 // for per-node priorities in the captured step graph.
 const void* form_k_kernel(bool fp32);
+const void* form_k_pos_kernel();
 bool is_k64_kernel(const void* f);
 const void* rod_dirs_kernel();
 cudaError_t refine_configure();

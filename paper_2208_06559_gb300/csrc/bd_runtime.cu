@@ -44,7 +44,8 @@ struct bd_ctx {
   double *uhat = nullptr, *T = nullptr, *rhs = nullptr, *scratch = nullptr, *obs = nullptr;
   float* Winv = nullptr;           // mixed: inverses of the diagonal tiles, [sum np][128]
   float2* fsplit = nullptr;        // mixed: (hi, lo) split of a mobility product's input, [sum np]
-  double* dF = nullptr;            // mixed: change of the forces in the last tension update
+  double* dT = nullptr;            // mixed: change of the tensions in the last tension update
+  float* G = nullptr;              // mixed: rod-space mobility C D C^T U, [3][mp][mp] per chain
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
   CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
@@ -161,8 +162,8 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
 
 int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, nullptr, c->fsplit,
-                       c->scratch, u, state, nullptr, s));
+    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->fsplit, c->scratch, u,
+                       state, s));
   else
     CK(launch_symv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
                            state, s));
@@ -179,15 +180,22 @@ void prof_mark(bd_ctx* c, int i, cudaStream_t s) {
 // own stream while D is factored and the Brownian displacement is formed.
 int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   int rc;
+  cudaStream_t sk = c->aux[0];
+  if (c->mixed) {
+    // K from the positions: the chain forks before the assembly
+    CK(cudaEventRecord(c->aev[0], s));
+    CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  }
   if ((rc = enqueue_assemble(c, s))) return rc;
   prof_mark(c, 1, s);
-  cudaStream_t sk = c->aux[0];
-  CK(cudaEventRecord(c->aev[0], s));
-  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  if (!c->mixed) {
+    CK(cudaEventRecord(c->aev[0], s));
+    CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  }
   CK(launch_rod_dirs(c->r, c->d_cd, c->n_chains, c->max_N, c->uhat, sk));
   if (c->mixed) {
-    CK(launch_form_k<float>((const float*)c->M, (float*)c->K, c->d_cd, c->n_chains, c->max_m,
-                            c->uhat, sk));
+    CK(launch_form_k_pos(c->r, (float*)c->K, c->G, c->d_cd, c->n_chains, c->max_m, c->uhat, c->ph.hstar,
+                         c->ph.a, sk));
     CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64,
                        c->status, sk));
   } else {
@@ -209,29 +217,39 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   return BD_OK;
 }
 
-// Mobility product of the tension iteration: in the mixed path plain FP32
-// sums while a chain's residual is large, compensated (FP64-level) after.
-int enqueue_newton_symv(bd_ctx* c, cudaStream_t s) {
-  if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->F, c->dF, c->fsplit,
-                       c->scratch, c->u, c->state, c->accurate, s));
-  else
-    return enqueue_symv(c, c->F, c->u, c->state, s);
+// One tension iteration.  FP64 path: the bead-space mobility product D F,
+// the residual from r(T) = r* + dt D F, the solve.  Mixed path: the rod-space
+// product w = G T (plain FP32 sums while a chain's residual is large,
+// compensated after, increments G dT once accurate), the residual from
+// Q(T) = Q* - dt w, the solve (which also records dT).
+int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
+  if (c->mixed) {
+    CK(launch_tension_products_g(c->G, c->d_cd, c->n_chains, c->max_mp, c->T, c->dT, c->u, c->state,
+                                 c->accurate, s));
+    CK(launch_newton_residual_g(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rhs, c->state, c->status,
+                                c->iters, c->accurate, s));
+    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph,
+                                  c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s, c->dT));
+    return BD_OK;
+  }
+  int rc;
+  if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+  CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
+                            c->status, c->iters, s));
+  CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph,
+                                 c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
   return BD_OK;
 }
 
-// One tension iteration: mobility product, residual and state update, solve.
-int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
-  int rc;
-  if ((rc = enqueue_newton_symv(c, s))) return rc;
-  CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                            c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
+// Commit the step: r <- r(T) for converged chains (mixed path: rebuilt from
+// the rods), step index advanced.
+int enqueue_finalize(bd_ctx* c, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph,
-                                  c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s, c->dF));
+    CK(launch_finalize_g(c->d_cd, c->n_chains, c->ph, c->rstar, c->u, c->F, c->r, c->state, c->status,
+                         c->args, s));
   else
-    CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph,
-                                   c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
+    CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status, c->args,
+                       s));
   return BD_OK;
 }
 
@@ -271,7 +289,7 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
     const bool kchain = c->mixed && (kp.func == form_k_kernel(true) || kp.func == rod_dirs_kernel() ||
-                                     is_k64_kernel(kp.func));
+                                     is_k64_kernel(kp.func) || kp.func == form_k_pos_kernel());
     cudaLaunchAttributeValue v;
     memset(&v, 0, sizeof(v));
     v.priority = kchain ? c->pr_low : c->pr_high;
@@ -370,8 +388,11 @@ int build_step_graph(bd_ctx* c) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
-  CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
-                     c->args, s));
+  if ((rc = enqueue_finalize(c, s))) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
   CK(cudaStreamEndCapture(s, &g));
   set_graph_priorities(c, g);
   set_graph_priorities(c, body);
@@ -393,8 +414,7 @@ int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
   for (int it = 0; it < c->direct_iters; ++it)
     if ((rc = enqueue_newton_iter(c, s))) return rc;
   prof_mark(c, 5, s);
-  CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status,
-                     c->args, s));
+  if ((rc = enqueue_finalize(c, s))) return rc;
   prof_mark(c, 6, s);
   return BD_OK;
 }
@@ -523,7 +543,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dF, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -667,7 +687,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
        (c->mixed || alloc(&c->Minv, (size_t)swrow * kSimtTile * c->elem));
   if (ok && c->mixed)
     ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
-         alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) && alloc((void**)&c->dF, b3) &&
+         alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) &&
+         alloc((void**)&c->dT, rr) && alloc((void**)&c->G, 3 * c->K_elems * sizeof(float)) &&
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
@@ -713,7 +734,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   }
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
       assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
-      k64_configure() != cudaSuccess)
+      k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -729,6 +750,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (c->mixed) {
     e1 = launch_fill_identity_border<float>((float*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
     e2 = launch_fill_identity_border<float>((float*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
+    if (e1 == cudaSuccess) e1 = cudaMemsetAsync(c->G, 0, 3 * c->K_elems * sizeof(float), s);
   } else {
     e1 = launch_fill_identity_border<double>((double*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
     e2 = launch_fill_identity_border<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
@@ -972,7 +994,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
     for (int it = 0; it < iters_max; ++it) {
       if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
       CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
-                                c->status, c->iters, nullptr, s));
+                                c->status, c->iters, s));
       CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
                                      c->ph, c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
     }

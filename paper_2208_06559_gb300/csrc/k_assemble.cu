@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "bd_internal.h"
+#include "rpy_dev.h"
 
 namespace bd {
 
@@ -20,26 +21,6 @@ constexpr int kElTile = 3 * kBeadTile;  // 96 x 96 elements per tile
 template <typename T>
 constexpr int assemble_smem() {
   return kElTile * (kElTile + 1) * (int)sizeof(T);
-}
-
-// Coefficients of D_ij = cI * I + cRR * R R^T for separation R (|R|^2 = R2).
-// Eq. (8) for R >= 2a, Eq. (9) for R < 2a, the overlap limit (h*/a) I at R = 0.
-template <typename C>
-__device__ __forceinline__ void rpy_coeffs(C R2, C hstar, C a, C& cI, C& cRR) {
-  const C Rn = sqrt(R2);
-  if (hstar == C(0)) {
-    cI = C(0);
-    cRR = C(0);
-  } else if (Rn >= C(2) * a) {
-    const C pref = C(0.75) * hstar / Rn;
-    const C a2R2 = a * a / R2;
-    cI = pref * (C(1) + C(2) / C(3) * a2R2);
-    cRR = pref * (C(1) - C(2) * a2R2) / R2;
-  } else {
-    const C pref = C(0.375) * hstar / a;
-    cI = pref * (C(8) / C(3) - C(0.75) * Rn / a);
-    cRR = (Rn > C(0)) ? pref * (C(0.25) / a) / Rn : C(0);
-  }
 }
 
 // FP32 path: the positions arrive split into (hi, lo) float pairs (rs), and

@@ -15,6 +15,7 @@
 //        moves with the explicit step and the new links are summed around it.
 // No tension solve, no rod-coupling matrix.
 #include "bd_internal.h"
+#include "block_dev.h"
 
 namespace bd {
 
@@ -54,67 +55,6 @@ __global__ void k_fraenkel_forces(const double* __restrict__ r, const ChainDesc*
 
 constexpr int kFrThreads = 1024;
 constexpr int kFrPer = 4;  // beads (and links) per thread: N <= 4096
-
-// Sum of a 3-vector over the block (result in every thread).
-__device__ __forceinline__ void block_sum3(double v[3], double (*red)[3]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) red[warp][c] = v[c];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double x = red[lane][c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[0][c] = x;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int c = 0; c < 3; ++c) v[c] = red[0][c];
-  __syncthreads();
-}
-
-// Exclusive prefix sum of a 3-vector over the threads of the block.
-__device__ __forceinline__ void block_exscan3(double v[3], double (*red)[3]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double inc[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    inc[c] = v[c];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double x = __shfl_up_sync(0xffffffffu, inc[c], o);
-      if (lane >= o) inc[c] += x;
-    }
-  }
-  if (lane == 31)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) red[warp][c] = inc[c];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double x = red[lane][c];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      red[lane][c] = x;  // inclusive scan of the warp totals
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int c = 0; c < 3; ++c) v[c] = inc[c] - v[c] + (warp > 0 ? red[warp - 1][c] : 0.0);
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(kFrThreads) k_fraenkel_update(double* __restrict__ r,
                                                                 const double* __restrict__ y,

@@ -14,6 +14,7 @@
 //   form_k: K_kl = u_k^T (D_kl - D_k,l+1 - D_k+1,l + D_k+1,l+1) u_l, the
 //          rod-coupling matrix of the tension solve.
 #include "bd_internal.h"
+#include "rpy_dev.h"
 
 namespace bd {
 
@@ -255,6 +256,132 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
   }
 }
 
+// K for the mixed path straight from the positions, so that it needs neither
+// D nor the assembly and runs beside it: per 32 x 32 rod tile (kt >= lt) the
+// RPY coefficients of the 33 x 33 bead pairs the tile touches (Eqs. (8)-(9),
+// FP32 from positions split into float pairs) are formed once in shared
+// memory, then with B_kl = D_k,l - D_k,l+1 - D_k+1,l + D_k+1,l+1 (= B_lk,
+// a symmetric 3 x 3 block; D_aa = I)
+//   G_kl = B_kl u_l,  G_lk = B_kl u_k  (the rod-space mobility C D C^T U,
+//                                        three planes [3][mp][mp], optional)
+//   K_kl = u_k . G_kl  (lower triangle).
+// K only preconditions the tension iteration; G, when formed, is the
+// mobility the mixed path's tension iteration uses (its FP32 rounding is a
+// ~1e-7 relative change of the model, far below the TF32 factor's).
+constexpr int KB = KR + 1;  // beads per tile side
+
+__global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r, float* __restrict__ K,
+                                                    float* __restrict__ G,
+                                                    const ChainDesc* __restrict__ cd,
+                                                    const double* __restrict__ uhat, float hstar, float arad) {
+  __shared__ float cI[KB][KB + 1], cRR[KB][KB + 1];
+  __shared__ float Rv[3][KB][KB + 1];
+  __shared__ float ph[2][KB][3], pl[2][KB][3];  // split positions: [0] k side, [1] l side
+  __shared__ float uk[KR][3], ul[KR][3];
+  __shared__ float St[3][KR][KR + 1];            // G_lk staged for a coalesced transposed store
+  const ChainDesc d = cd[blockIdx.y];
+  const int m = d.m, N = d.N;
+  const int TK = (m + KR - 1) / KR;
+  const int p = blockIdx.x;
+  if (p >= TK * (TK + 1) / 2) return;
+  int kt = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while (kt * (kt + 1) / 2 > p) --kt;
+  while ((kt + 1) * (kt + 2) / 2 <= p) ++kt;
+  const int lt = p - kt * (kt + 1) / 2;  // lt <= kt
+  const int t = threadIdx.x;
+  const double* rc = r + 3 * d.boff;
+  if (t < 2 * KB * 3) {
+    const int side = t / (KB * 3), e = t % (KB * 3), bead = e / 3, q = e % 3;
+    const int gb = (side == 0 ? KR * kt : KR * lt) + bead;
+    const double v = gb < N ? rc[3 * gb + q] : 0.0;
+    const float h = (float)v;
+    ph[side][bead][q] = h;
+    pl[side][bead][q] = (float)(v - (double)h);
+  }
+  if (t < KR) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      uk[t][q] = (KR * kt + t < m) ? (float)uhat[3 * (d.roff + KR * kt + t) + q] : 0.0f;
+      ul[t][q] = (KR * lt + t < m) ? (float)uhat[3 * (d.roff + KR * lt + t) + q] : 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < KB * KB; e += blockDim.x) {
+    const int x = e / KB, y = e % KB;
+    const int a = KR * kt + x, b = KR * lt + y;
+    float ci = 0.0f, cr = 0.0f, R[3] = {0.0f, 0.0f, 0.0f};
+    if (a < N && b < N) {
+      if (a == b) {
+        ci = 1.0f;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) R[q] = (ph[0][x][q] - ph[1][y][q]) + (pl[0][x][q] - pl[1][y][q]);
+        rpy_coeffs<float>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, arad, ci, cr);
+      }
+    }
+    cI[x][y] = ci;
+    cRR[x][y] = cr;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Rv[q][x][y] = R[q];
+  }
+  __syncthreads();
+  const long long mp = d.mp;
+  float* Gc = G ? G + 3 * d.koff : nullptr;  // plane q at Gc + q mp^2
+  for (int e = t; e < KR * KR; e += blockDim.x) {
+    const int ia = e / KR, ib = e % KR;  // rod k = 32 kt + ia, rod l = 32 lt + ib
+    const int k = KR * kt + ia, l = KR * lt + ib;
+    const bool valid = k < m && l < m && l <= k;
+    const float u0 = uk[ia][0], u1 = uk[ia][1], u2 = uk[ia][2];
+    const float v0 = ul[ib][0], v1 = ul[ib][1], v2 = ul[ib][2];
+    float bv[3] = {0.0f, 0.0f, 0.0f}, bu[3] = {0.0f, 0.0f, 0.0f};  // B u_l, B u_k
+#pragma unroll
+    for (int da = 0; da < 2; ++da)
+#pragma unroll
+      for (int db = 0; db < 2; ++db) {
+        const int x = ia + da, y = ib + db;
+        const float sg = (da == db) ? 1.0f : -1.0f;
+        const float R0 = Rv[0][x][y], R1 = Rv[1][x][y], R2 = Rv[2][x][y];
+        const float ci = sg * cI[x][y], cr = sg * cRR[x][y];
+        const float Rv_ = cr * (R0 * v0 + R1 * v1 + R2 * v2), Ru = cr * (R0 * u0 + R1 * u1 + R2 * u2);
+        bv[0] += ci * v0 + Rv_ * R0;
+        bv[1] += ci * v1 + Rv_ * R1;
+        bv[2] += ci * v2 + Rv_ * R2;
+        bu[0] += ci * u0 + Ru * R0;
+        bu[1] += ci * u1 + Ru * R1;
+        bu[2] += ci * u2 + Ru * R2;
+      }
+    if (valid) {
+      K[d.koff + (long long)k * mp + l] = u0 * bv[0] + u1 * bv[1] + u2 * bv[2];
+      if (Gc) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Gc[q * mp * mp + (long long)k * mp + l] = bv[q];
+      }
+    }
+    if (Gc) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) St[q][ia][ib] = (valid && l < k) ? bu[q] : 0.0f;
+    }
+  }
+  if (!Gc) return;
+  __syncthreads();
+  // G_lk for the tile's pairs with l < k: row l, column k (transposed store)
+  for (int e = t; e < KR * KR; e += blockDim.x) {
+    const int ib = e / KR, ia = e % KR;
+    const int k = KR * kt + ia, l = KR * lt + ib;
+    if (k < m && l < m && l < k) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Gc[q * mp * mp + (long long)l * mp + k] = St[q][ia][ib];
+    }
+  }
+}
+
+cudaError_t launch_form_k_pos(const double* r, float* K, float* G, const ChainDesc* cd, int n_chains,
+                              int max_m, const double* u, double hstar, double a, cudaStream_t s) {
+  const int TK = ceil_div(max_m, KR);
+  k_form_k_pos<<<dim3(TK * (TK + 1) / 2, n_chains), 256, 0, s>>>(r, K, G, cd, u, (float)hstar, (float)a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_form_k(const T* M, T* K, const ChainDesc* cd, int n_chains, int max_m,
                           const double* u, cudaStream_t s) {
@@ -324,15 +451,13 @@ __device__ __forceinline__ void upper_tile_of(int p, int& bi, int& bj) {
 }
 
 __global__ void k_split_f2(const ChainDesc* __restrict__ cd, const double* __restrict__ f,
-                           const double* __restrict__ df, float2* __restrict__ fs,
-                           const int* __restrict__ state, const int* __restrict__ mode) {
+                           float2* __restrict__ fs, const int* __restrict__ state) {
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.np) return;
-  const double* src = (mode && mode[c] >= MOB_INC_DF) ? df : f;
-  const double v = (e < d.n) ? src[3 * d.boff + e] : 0.0;
+  const double v = (e < d.n) ? f[3 * d.boff + e] : 0.0;
   const float h = (float)v;
   fs[d.swrow + e] = make_float2(h, (float)(v - (double)h));
 }
@@ -368,16 +493,12 @@ __device__ __forceinline__ bool symv_tile(int id, int tpc, const ChainDesc* __re
 
 // Persistent: CTA b takes tiles b, b + grid, ...; the next tile (and its two
 // f segments) is copied into the other shared-memory stage while the current
-// one is summed.  `mode` (per chain, may be NULL = double-float):
-// MOB_FULL_F32 and MOB_INC_F32 select plain FP32 sums (relative error ~1e-7),
-// used by the tension iteration while its residual is large, and for
-// increments once they are small.
+// one is summed.
 __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict__ M,
                                                         const ChainDesc* __restrict__ cd, int n_chains,
                                                         int tpc, const float2* __restrict__ fs,
                                                         float2* __restrict__ P,
-                                                        const int* __restrict__ state,
-                                                        const int* __restrict__ mode) {
+                                                        const int* __restrict__ state) {
   __shared__ __align__(16) float S[2][SF][SFP];
   __shared__ __align__(16) float2 fr[2][SF], fc[2][SF];  // (hi, lo) of f at the tile's rows / columns
   const int t = threadIdx.x;
@@ -427,34 +548,7 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
       float2* Pc = P + d.soff;
       const float4* fc4 = reinterpret_cast<const float4*>(fc[buf]);  // (h0, l0, h1, l1)
       const float4* fr4 = reinterpret_cast<const float4*>(fr[buf]);
-      const int md = mode ? mode[c] : MOB_FULL_DF;
-      if (md == MOB_FULL_F32 || md == MOB_INC_F32) {
-        if (t < SF) {
-          float acc = 0.f;
-#pragma unroll 4
-          for (int q4 = 0; q4 < SF / 4; ++q4) {
-            const float4 v = *reinterpret_cast<const float4*>(&Sb[t][4 * q4]);
-            const float4 f01 = fc4[2 * q4], f23 = fc4[2 * q4 + 1];
-            acc = fmaf(v.x, f01.x, acc);
-            acc = fmaf(v.y, f01.z, acc);
-            acc = fmaf(v.z, f23.x, acc);
-            acc = fmaf(v.w, f23.z, acc);
-          }
-          Pc[bj * ld + r0 + t] = make_float2(acc, 0.f);
-        } else if (!diag) {
-          const int q = t - SF;
-          float acc = 0.f;
-#pragma unroll 4
-          for (int r = 0; r < SF; r += 4) {
-            const float4 f01 = fr4[r >> 1], f23 = fr4[(r >> 1) + 1];
-            acc = fmaf(Sb[r][q], f01.x, acc);
-            acc = fmaf(Sb[r + 1][q], f01.z, acc);
-            acc = fmaf(Sb[r + 2][q], f23.x, acc);
-            acc = fmaf(Sb[r + 3][q], f23.z, acc);
-          }
-          Pc[bi * ld + c0 + q] = make_float2(acc, 0.f);
-        }
-      } else {
+      {
         if (t < SF) {
           DF acc{0.f, 0.f};
 #pragma unroll 4
@@ -488,8 +582,7 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
 }
 
 __global__ void k_symv_reduce_df(const ChainDesc* __restrict__ cd, const float2* __restrict__ P,
-                                 double* __restrict__ u, const int* __restrict__ state,
-                                 const int* __restrict__ mode) {
+                                 double* __restrict__ u, const int* __restrict__ state) {
   const int c = blockIdx.y;
   if (state && state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
@@ -506,25 +599,21 @@ __global__ void k_symv_reduce_df(const ChainDesc* __restrict__ cd, const float2*
     lo += ((hi - (s - bp)) + (v.x - bp)) + v.y;
     hi = s;
   }
-  const double v = (double)hi + (double)lo;
-  if (mode && mode[c] >= MOB_INC_DF)
-    u[3 * d.boff + row] += v;
-  else
-    u[3 * d.boff + row] = v;
+  u[3 * d.boff + row] = (double)hi + (double)lo;
 }
 
 cudaError_t launch_split_f2(const ChainDesc* cd, int n_chains, int max_np, const double* v,
                             float2* out, const int* state, cudaStream_t s) {
-  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, v, nullptr, out, state, nullptr);
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, v, out, state);
   return cudaGetLastError();
 }
 
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
-                            const double* f, const double* df, float2* fsplit, double* scratch,
-                            double* u, const int* state, const int* mode, cudaStream_t s) {
+                            const double* f, float2* fsplit, double* scratch, double* u,
+                            const int* state, cudaStream_t s) {
   const int TSn = ceil_div(max_np, SF);
   float2* P = reinterpret_cast<float2*>(scratch);
-  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, f, df, fsplit, state, mode);
+  k_split_f2<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, f, fsplit, state);
   static int n_sm = 0;
   if (!n_sm) {
     int dev = 0;
@@ -535,10 +624,12 @@ cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, i
   const int tpc = TSn * (TSn + 1) / 2;
   const long long total = (long long)tpc * n_chains;
   const int grid = (int)(total < (long long)kSymvCtasPerSm * n_sm ? total : (long long)kSymvCtasPerSm * n_sm);
-  k_symv_tiles_f32<<<grid, 128, 0, s>>>(M, cd, n_chains, tpc, fsplit, P, state, mode);
-  k_symv_reduce_df<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, P, u, state, mode);
+  k_symv_tiles_f32<<<grid, 128, 0, s>>>(M, cd, n_chains, tpc, fsplit, P, state);
+  k_symv_reduce_df<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, P, u, state);
   return cudaGetLastError();
 }
+
+const void* form_k_pos_kernel() { return (const void*)k_form_k_pos; }
 
 const void* form_k_kernel(bool fp32) {
   return fp32 ? (const void*)k_form_k<float> : (const void*)k_form_k<double>;

@@ -347,7 +347,7 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
   e = cudaEventRecord(ev[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e != cudaSuccess) return e;
-  e = launch_symv_f32(M, cd, n_chains, max_np, z, nullptr, fsplit, scratch, w, nullptr, nullptr, s);
+  e = launch_symv_f32(M, cd, n_chains, max_np, z, fsplit, scratch, w, nullptr, s);
   if (e != cudaSuccess) return e;
   k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);
   return cudaGetLastError();

@@ -157,8 +157,7 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
                                                          double* __restrict__ rhs,
                                                          int* __restrict__ state,
                                                          int* __restrict__ status,
-                                                         const int* __restrict__ iters,
-                                                         int* __restrict__ accurate) {
+                                                         const int* __restrict__ iters) {
   __shared__ double red[32];
   const int c = blockIdx.x;
   const int st = state[c];
@@ -183,35 +182,22 @@ __global__ void __launch_bounds__(256) k_newton_residual(const double* __restric
   gmax = block_max(gmax, red);
   if (threadIdx.x == 0) {
     int ns = st;
-    const bool acc_now = !accurate || accurate[c] != MOB_FULL_F32;
     if (st == NS_EXTRA) {
       ns = NS_DONE;
-    } else if (gmax <= ph.tol && acc_now) {
+    } else if (gmax <= ph.tol) {
       ns = NS_EXTRA;
     } else if (iters[c] >= ph.max_newton || !(gmax < INFINITY)) {
       ns = NS_FAILED;
       atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
     }
     state[c] = ns;
-    // The residual decides convergence only when it was evaluated accurately.
-    // Mobility products: plain FP32 while the residual is large, then one
-    // full double-float product, then increments D (F_new - F_old) of size
-    // ~|g|: double-float while |g| >= 1e-10, plain FP32 below (error ~1e-7
-    // of an increment below 1e-10, far under the tolerance).
-    if (accurate) {
-      const int md = accurate[c];
-      if (md == MOB_FULL_F32)
-        accurate[c] = (gmax < 1e-5) ? MOB_FULL_DF : MOB_FULL_F32;
-      else
-        accurate[c] = (gmax < 1e-10) ? MOB_INC_F32 : MOB_INC_DF;
-    }
   }
 }
 
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs, int* state,
-                                   int* status, const int* iters, int* accurate, cudaStream_t s) {
-  k_newton_residual<<<n_chains, 256, 0, s>>>(rstar, u, cd, ph, rT, rhs, state, status, iters, accurate);
+                                   int* status, const int* iters, cudaStream_t s) {
+  k_newton_residual<<<n_chains, 256, 0, s>>>(rstar, u, cd, ph, rT, rhs, state, status, iters);
   return cudaGetLastError();
 }
 
@@ -346,121 +332,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
 // Two (forward) and three (backward) barriers per block.
 constexpr int kS64 = 64;
 
-__global__ void __launch_bounds__(kSolveThreads) k_newton_solve_f32(const float* __restrict__ K,
-                                                                  const float* __restrict__ Kinv,
-                                                                  const ChainDesc* __restrict__ cd, Phys ph,
-                                                                  const double* __restrict__ uhat,
-                                                                  double* __restrict__ rhs,
-                                                                  double* __restrict__ Tn,
-                                                                  double* __restrict__ F,
-                                                                  int* __restrict__ state,
-                                                                  int* __restrict__ iters,
-                                                                  double* __restrict__ dF) {
-  extern __shared__ __align__(16) uint8_t ns_smem[];
-  float* zs = reinterpret_cast<float*>(ns_smem);  // [64 nb]: z, then x
-  __shared__ __align__(16) float sblk[kS64];
-  __shared__ float red[kS64][kS64 + 1];
-  const int c = blockIdx.x;
-  const int st = state[c];
-  if (st != NS_ACTIVE && st != NS_EXTRA) return;
-  const ChainDesc d = cd[c];
-  const int m = d.m;
-  const long long mp = d.mp;
-  const float* L = K + d.koff;
-  const float* Wb = Kinv + d.kwrow * kS64;
-  const int t = threadIdx.x, r = t >> 4, g = t & 15;
-  const int nb = (m + kS64 - 1) / kS64;
-  for (int e = t; e < nb * kS64; e += kSolveThreads) zs[e] = (e < m) ? (float)rhs[d.roff + e] : 0.0f;
-  __syncthreads();
-  // ---- forward
-  for (int b = 0; b < nb; ++b) {
-    const int row = kS64 * b + r;
-    const float4 wv = *reinterpret_cast<const float4*>(Wb + (long long)row * kS64 + 4 * g);
-    float acc = 0.0f;
-    if (row < m) {
-      const float* Lr = L + (long long)row * mp + 4 * g;
-#pragma unroll 4
-      for (int j = 0; j < b; ++j) {
-        const float4 lv = *reinterpret_cast<const float4*>(Lr + kS64 * j);
-        const float4 zv = *reinterpret_cast<const float4*>(zs + kS64 * j + 4 * g);
-        acc = fmaf(lv.x, zv.x, acc);
-        acc = fmaf(lv.y, zv.y, acc);
-        acc = fmaf(lv.z, zv.z, acc);
-        acc = fmaf(lv.w, zv.w, acc);
-      }
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (g == 0) sblk[r] = (row < m) ? zs[row] - acc : 0.0f;
-    __syncthreads();
-    const float4 sv = *reinterpret_cast<const float4*>(sblk + 4 * g);
-    float zr = wv.x * sv.x + wv.y * sv.y + wv.z * sv.z + wv.w * sv.w;
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) zr += __shfl_xor_sync(0xffffffffu, zr, o);
-    if (g == 0) zs[row] = (row < m) ? zr : 0.0f;
-    __syncthreads();
-  }
-  // ---- backward
-  for (int b = nb - 1; b >= 0; --b) {
-    const int c0 = kS64 * b;
-    float w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w[q] = Wb[(long long)(c0 + 4 * g + q) * kS64 + r];  // W_b[4g+q][r]
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const float* Lc = L + c0 + 4 * g;
-#pragma unroll 4
-    for (int R = c0 + kS64 + r; R < m; R += kS64) {
-      const float4 lv = *reinterpret_cast<const float4*>(Lc + (long long)R * mp);
-      const float x = zs[R];
-      a0 = fmaf(lv.x, x, a0);
-      a1 = fmaf(lv.y, x, a1);
-      a2 = fmaf(lv.z, x, a2);
-      a3 = fmaf(lv.w, x, a3);
-    }
-    red[r][4 * g] = a0;
-    red[r][4 * g + 1] = a1;
-    red[r][4 * g + 2] = a2;
-    red[r][4 * g + 3] = a3;
-    __syncthreads();
-    {
-      const int cc = t >> 4, part = t & 15;  // column cc, row groups 4 part .. 4 part + 3
-      float v = red[4 * part][cc] + red[4 * part + 1][cc] + red[4 * part + 2][cc] + red[4 * part + 3][cc];
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (part == 0) sblk[cc] = (c0 + cc < m) ? zs[c0 + cc] - v : 0.0f;
-    }
-    __syncthreads();
-    const float4 sv = *reinterpret_cast<const float4*>(sblk + 4 * g);
-    float xr = w[0] * sv.x + w[1] * sv.y + w[2] * sv.z + w[3] * sv.w;  // sum_c W_b[c][r] s_c
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) xr += __shfl_xor_sync(0xffffffffu, xr, o);
-    if (g == 0 && c0 + r < m) zs[c0 + r] = xr;  // zs[c0 ..] was last read before the barrier above
-    __syncthreads();
-  }
-  // T += delta
-  for (int k = t; k < m; k += blockDim.x) Tn[d.roff + k] += (double)zs[k];
-  __syncthreads();
-  // F(T) and F(delta)
-  for (int i = t; i < d.N; i += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double f = 0.0, g = 0.0;
-      if (i < m) {
-        f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
-        g += (double)zs[i] * uhat[3 * (d.roff + i) + q];
-      }
-      if (i > 0) {
-        f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
-        g -= (double)zs[i - 1] * uhat[3 * (d.roff + i - 1) + q];
-      }
-      F[3 * (d.boff + i) + q] = f;
-      if (dF) dF[3 * (d.boff + i) + q] = g;
-    }
-  }
-  if (t == 0) iters[c] += 1;
-}
-
-// The same solve split over a cluster of two CTAs per chain: in every block
+// The solve runs on a cluster of two CTAs per chain: in every block
 // step each CTA sums half of the loads (alternate 64-wide column blocks in
 // the forward sweep, alternate 64-row groups in the backward sweep), the two
 // partial sums are exchanged through distributed shared memory (double
@@ -471,7 +343,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSolveThreads)
     k_newton_solve_f32c(const float* __restrict__ K, const float* __restrict__ Kinv,
                         const ChainDesc* __restrict__ cd, Phys ph, const double* __restrict__ uhat,
                         double* __restrict__ rhs, double* __restrict__ Tn, double* __restrict__ F,
-                        int* __restrict__ state, int* __restrict__ iters, double* __restrict__ dF) {
+                        int* __restrict__ state, int* __restrict__ iters, double* __restrict__ dT) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -574,24 +446,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSolveThreads)
   }
   cl.sync();  // no CTA leaves while its partner may still read its shared memory
   if (rank != 0) return;
-  // T += delta
-  for (int k = t; k < m; k += blockDim.x) Tn[d.roff + k] += (double)zs[k];
+  // T += delta (and delta itself for incremental products in rod space)
+  for (int k = t; k < m; k += blockDim.x) {
+    Tn[d.roff + k] += (double)zs[k];
+    if (dT) dT[d.roff + k] = (double)zs[k];
+  }
   __syncthreads();
-  // F(T) and F(delta)
+  // F(T)
   for (int i = t; i < d.N; i += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      double f = 0.0, gg = 0.0;
-      if (i < m) {
-        f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
-        gg += (double)zs[i] * uhat[3 * (d.roff + i) + q];
-      }
-      if (i > 0) {
-        f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
-        gg -= (double)zs[i - 1] * uhat[3 * (d.roff + i - 1) + q];
-      }
+      double f = 0.0;
+      if (i < m) f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
+      if (i > 0) f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
       F[3 * (d.boff + i) + q] = f;
-      if (dF) dF[3 * (d.boff + i) + q] = gg;
     }
   }
   if (t == 0) iters[c] += 1;
@@ -606,10 +474,10 @@ constexpr int solve_block() {
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F, int* state,
-                                int* iters, cudaStream_t s, double* dF) {
+                                int* iters, cudaStream_t s, double* dT) {
   if constexpr (sizeof(T) == 4)
     k_newton_solve_f32c<<<2 * n_chains, kSolveThreads, kSolveMaxM * sizeof(float), s>>>(
-        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters, dF);
+        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters, dT);
   else
     k_newton_solve<T, solve_block<T>()><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(
         K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters);
@@ -764,9 +632,6 @@ cudaError_t tension_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double, 32>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(kSolveMaxM * sizeof(double)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_newton_solve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSolveMaxM * sizeof(float)));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_newton_solve_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSolveMaxM * sizeof(float)));
