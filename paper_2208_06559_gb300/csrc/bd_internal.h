@@ -114,12 +114,22 @@ cudaError_t launch_predictor(const double* r, const double* y, const ChainDesc* 
 cudaError_t launch_newton_residual(const double* rstar, const double* u, const ChainDesc* cd,
                                    int n_chains, Phys ph, double* rT, double* rhs,
                                    int* state, int* status, const int* iters, cudaStream_t s);
-// dT (optional, FP32 factor only): the update itself, per rod -- for the
-// incremental rod-space products.
+// FP64 path (32-wide blocks of K's factor and their inverses).
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F,
-                                int* state, int* iters, cudaStream_t s, double* dT = nullptr);
+                                int* state, int* iters, cudaStream_t s);
+// Mixed path, tension solve with 256-wide super-blocks (k_solve_sb.cu): the
+// inverses of the diagonal super-blocks of K's factor, V ([sum mp][256] FP32,
+// chain offset kwrow * 256, zero above the diagonal), once per step; then the
+// solve itself, T += delta, dT = delta (optional), F(T).
+cudaError_t launch_sb_inverse(const float* K, const float* Kinv, float* V, const ChainDesc* cd, int n_chains,
+                              int max_mp, cudaStream_t s);
+cudaError_t launch_newton_solve_sb(const float* K, const float* V, const ChainDesc* cd, int n_chains, Phys ph,
+                                   const double* uhat, const double* rhs, double* Tn, double* F, int* state,
+                                   int* iters, double* dT, cudaStream_t s);
+bool is_sb_inverse_kernel(const void* f);
+cudaError_t solve_sb_configure();
 // Rod-space tension iteration of the mixed path (k_gmode.cu).
 cudaError_t launch_tension_products_g(const float* G, const ChainDesc* cd, int n_chains, int max_mp,
                                       const double* T, const double* dT, double* w, const int* state,

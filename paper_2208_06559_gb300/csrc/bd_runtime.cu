@@ -46,6 +46,7 @@ struct bd_ctx {
   float2* fsplit = nullptr;        // mixed: (hi, lo) split of a mobility product's input, [sum np]
   double* dT = nullptr;            // mixed: change of the tensions in the last tension update
   float* G = nullptr;              // mixed: rod-space mobility C D C^T U, [3][mp][mp] per chain
+  float* Vsb = nullptr;            // mixed: inverses of the 256-wide diagonal super-blocks of K's factor
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
   CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
@@ -198,6 +199,7 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
                          c->ph.a, sk));
     CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64,
                        c->status, sk));
+    CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
   } else {
     CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
                              c->uhat, sk));
@@ -228,8 +230,8 @@ int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
                                  c->accurate, s));
     CK(launch_newton_residual_g(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rhs, c->state, c->status,
                                 c->iters, c->accurate, s));
-    CK(launch_newton_solve<float>((const float*)c->K, (const float*)c->Kinv, c->d_cd, c->n_chains, c->ph,
-                                  c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s, c->dT));
+    CK(launch_newton_solve_sb((const float*)c->K, c->Vsb, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs, c->T,
+                              c->F, c->state, c->iters, c->dT, s));
     return BD_OK;
   }
   int rc;
@@ -289,7 +291,8 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
     const bool kchain = c->mixed && (kp.func == form_k_kernel(true) || kp.func == rod_dirs_kernel() ||
-                                     is_k64_kernel(kp.func) || kp.func == form_k_pos_kernel());
+                                     is_k64_kernel(kp.func) || kp.func == form_k_pos_kernel() ||
+                                     is_sb_inverse_kernel(kp.func));
     cudaLaunchAttributeValue v;
     memset(&v, 0, sizeof(v));
     v.priority = kchain ? c->pr_low : c->pr_high;
@@ -543,7 +546,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -689,6 +692,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     ok = alloc((void**)&c->Winv, (size_t)wrow * kMixedTile * sizeof(float)) &&
          alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) &&
          alloc((void**)&c->dT, rr) && alloc((void**)&c->G, 3 * c->K_elems * sizeof(float)) &&
+         alloc((void**)&c->Vsb, (size_t)kwrow * 256 * sizeof(float)) &&
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
@@ -734,7 +738,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   }
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
       assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
-      k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess)
+      k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess ||
+      solve_sb_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -751,6 +756,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     e1 = launch_fill_identity_border<float>((float*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
     e2 = launch_fill_identity_border<float>((float*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
     if (e1 == cudaSuccess) e1 = cudaMemsetAsync(c->G, 0, 3 * c->K_elems * sizeof(float), s);
+    if (e1 == cudaSuccess) e1 = cudaMemsetAsync(c->Vsb, 0, (size_t)kwrow * 256 * sizeof(float), s);
   } else {
     e1 = launch_fill_identity_border<double>((double*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
     e2 = launch_fill_identity_border<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);

@@ -15,7 +15,6 @@
 // followed by one more update, exactly the stopping rule of the oracle's
 // Newton.  The root is the same; the convergence is linear with a rate of
 // order |Q - u| ~ sqrt(dt) instead of quadratic.
-#include <cooperative_groups.h>
 #include <math.h>
 
 #include "bd_internal.h"
@@ -319,168 +318,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_newton_solve(const T* __restr
   if (t == 0) iters[c] += 1;
 }
 
-// Mixed path (FP32 factor, 64-wide blocks): every block step is one pass of
-// independent 16-byte loads, 16 threads per 64-wide row segment.
-//   forward  L z = rhs, block b: thread (r, g) = (t / 16, t % 16) sums
-//            L[64b + r][64j + 4g ..] z[64j + 4g ..] over j < b, the 16 lanes
-//            reduce, s_b = rhs_b - sum; z_b = W_b s_b (row r of W_b as one
-//            vector per thread, issued before the sums).
-//   backward L^T x = z, block b from the last: thread (rg, g) sums
-//            L[R][64b + 4g ..] x[R] over rows R = 64(b+1) + rg, +64, ...;
-//            partial sums are reduced through shared memory,
-//            x_b = W_b^T (z_b - sum).
-// Two (forward) and three (backward) barriers per block.
-constexpr int kS64 = 64;
-
-// The solve runs on a cluster of two CTAs per chain: in every block
-// step each CTA sums half of the loads (alternate 64-wide column blocks in
-// the forward sweep, alternate 64-row groups in the backward sweep), the two
-// partial sums are exchanged through distributed shared memory (double
-// buffered, one cluster barrier per block step) and added in a fixed order,
-// and both CTAs apply the diagonal-block inverse, so their copies of z and x
-// stay identical.  Rank 0 writes the results.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSolveThreads)
-    k_newton_solve_f32c(const float* __restrict__ K, const float* __restrict__ Kinv,
-                        const ChainDesc* __restrict__ cd, Phys ph, const double* __restrict__ uhat,
-                        double* __restrict__ rhs, double* __restrict__ Tn, double* __restrict__ F,
-                        int* __restrict__ state, int* __restrict__ iters, double* __restrict__ dT) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  extern __shared__ __align__(16) uint8_t ns_smem[];
-  float* zs = reinterpret_cast<float*>(ns_smem);  // [64 nb]: z, then x
-  __shared__ __align__(16) float sblk[kS64];
-  __shared__ float red[kS64][kS64 + 1];
-  __shared__ float part[2][kS64];  // this CTA's partial sums, by block-step parity
-  const int c = blockIdx.x >> 1;
-  const int st = state[c];
-  if (st != NS_ACTIVE && st != NS_EXTRA) return;  // the same for both CTAs of the cluster
-  const ChainDesc d = cd[c];
-  const int m = d.m;
-  const long long mp = d.mp;
-  const float* L = K + d.koff;
-  const float* Wb = Kinv + d.kwrow * kS64;
-  const int t = threadIdx.x, r = t >> 4, g = t & 15;
-  const int nb = (m + kS64 - 1) / kS64;
-  for (int e = t; e < nb * kS64; e += kSolveThreads) zs[e] = (e < m) ? (float)rhs[d.roff + e] : 0.0f;
-  __syncthreads();
-  int par = 0;
-  // ---- forward
-  for (int b = 0; b < nb; ++b, par ^= 1) {
-    const int row = kS64 * b + r;
-    const float4 wv = *reinterpret_cast<const float4*>(Wb + (long long)row * kS64 + 4 * g);
-    float acc = 0.0f;
-    if (row < m) {
-      const float* Lr = L + (long long)row * mp + 4 * g;
-#pragma unroll 4
-      for (int j = rank; j < b; j += 2) {
-        const float4 lv = *reinterpret_cast<const float4*>(Lr + kS64 * j);
-        const float4 zv = *reinterpret_cast<const float4*>(zs + kS64 * j + 4 * g);
-        acc = fmaf(lv.x, zv.x, acc);
-        acc = fmaf(lv.y, zv.y, acc);
-        acc = fmaf(lv.z, zv.z, acc);
-        acc = fmaf(lv.w, zv.w, acc);
-      }
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (g == 0) part[par][r] = acc;
-    cl.sync();
-    if (g == 0) {
-      const float* other = cl.map_shared_rank(&part[par][0], rank ^ 1);
-      const float p0 = rank == 0 ? part[par][r] : other[r];
-      const float p1 = rank == 0 ? other[r] : part[par][r];
-      sblk[r] = (row < m) ? zs[row] - (p0 + p1) : 0.0f;
-    }
-    __syncthreads();
-    const float4 sv = *reinterpret_cast<const float4*>(sblk + 4 * g);
-    float zr = wv.x * sv.x + wv.y * sv.y + wv.z * sv.z + wv.w * sv.w;
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) zr += __shfl_xor_sync(0xffffffffu, zr, o);
-    if (g == 0) zs[row] = (row < m) ? zr : 0.0f;
-    __syncthreads();
-  }
-  // ---- backward
-  for (int b = nb - 1; b >= 0; --b, par ^= 1) {
-    const int c0 = kS64 * b;
-    float w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w[q] = Wb[(long long)(c0 + 4 * g + q) * kS64 + r];  // W_b[4g+q][r]
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    const float* Lc = L + c0 + 4 * g;
-#pragma unroll 4
-    for (int R = c0 + kS64 * (1 + rank) + r; R < m; R += 2 * kS64) {
-      const float4 lv = *reinterpret_cast<const float4*>(Lc + (long long)R * mp);
-      const float x = zs[R];
-      a0 = fmaf(lv.x, x, a0);
-      a1 = fmaf(lv.y, x, a1);
-      a2 = fmaf(lv.z, x, a2);
-      a3 = fmaf(lv.w, x, a3);
-    }
-    red[r][4 * g] = a0;
-    red[r][4 * g + 1] = a1;
-    red[r][4 * g + 2] = a2;
-    red[r][4 * g + 3] = a3;
-    __syncthreads();
-    {
-      const int cc = t >> 4, pt = t & 15;  // column cc, row groups 4 pt .. 4 pt + 3
-      float v = red[4 * pt][cc] + red[4 * pt + 1][cc] + red[4 * pt + 2][cc] + red[4 * pt + 3][cc];
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (pt == 0) part[par][cc] = v;
-    }
-    cl.sync();
-    if (t < kS64) {
-      const float* other = cl.map_shared_rank(&part[par][0], rank ^ 1);
-      const float p0 = rank == 0 ? part[par][t] : other[t];
-      const float p1 = rank == 0 ? other[t] : part[par][t];
-      sblk[t] = (c0 + t < m) ? zs[c0 + t] - (p0 + p1) : 0.0f;
-    }
-    __syncthreads();
-    const float4 sv = *reinterpret_cast<const float4*>(sblk + 4 * g);
-    float xr = w[0] * sv.x + w[1] * sv.y + w[2] * sv.z + w[3] * sv.w;  // sum_c W_b[c][r] s_c
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) xr += __shfl_xor_sync(0xffffffffu, xr, o);
-    if (g == 0 && c0 + r < m) zs[c0 + r] = xr;  // zs[c0 ..] was last read before the barrier above
-    __syncthreads();
-  }
-  cl.sync();  // no CTA leaves while its partner may still read its shared memory
-  if (rank != 0) return;
-  // T += delta (and delta itself for incremental products in rod space)
-  for (int k = t; k < m; k += blockDim.x) {
-    Tn[d.roff + k] += (double)zs[k];
-    if (dT) dT[d.roff + k] = (double)zs[k];
-  }
-  __syncthreads();
-  // F(T)
-  for (int i = t; i < d.N; i += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double f = 0.0;
-      if (i < m) f += Tn[d.roff + i] * uhat[3 * (d.roff + i) + q];
-      if (i > 0) f -= Tn[d.roff + i - 1] * uhat[3 * (d.roff + i - 1) + q];
-      F[3 * (d.boff + i) + q] = f;
-    }
-  }
-  if (t == 0) iters[c] += 1;
-}
-
-// the FP64 path factors K with 32-wide tiles, the mixed path with 64-wide ones
-template <typename T>
-constexpr int solve_block() {
-  return sizeof(T) == 8 ? 32 : 64;
-}
-
 template <typename T>
 cudaError_t launch_newton_solve(const T* K, const T* Kinv, const ChainDesc* cd, int n_chains, Phys ph,
                                 const double* uhat, double* rhs, double* Tn, double* F, int* state,
-                                int* iters, cudaStream_t s, double* dT) {
-  if constexpr (sizeof(T) == 4)
-    k_newton_solve_f32c<<<2 * n_chains, kSolveThreads, kSolveMaxM * sizeof(float), s>>>(
-        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters, dT);
-  else
-    k_newton_solve<T, solve_block<T>()><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(
-        K, Kinv, cd, ph, uhat, rhs, Tn, F, state, iters);
+                                int* iters, cudaStream_t s) {
+  k_newton_solve<T, 32><<<n_chains, kSolveThreads, kSolveMaxM * sizeof(T), s>>>(K, Kinv, cd, ph, uhat, rhs,
+                                                                                Tn, F, state, iters);
   return cudaGetLastError();
 }
 
@@ -621,10 +464,7 @@ cudaError_t launch_set_args(StepArgs* args, const double* noise, long long strid
 
 template cudaError_t launch_newton_solve<double>(const double*, const double*, const ChainDesc*, int,
                                                  Phys, const double*, double*, double*, double*,
-                                                 int*, int*, cudaStream_t, double*);
-template cudaError_t launch_newton_solve<float>(const float*, const float*, const ChainDesc*, int,
-                                                Phys, const double*, double*, double*, double*, int*,
-                                                int*, cudaStream_t, double*);
+                                                 int*, int*, cudaStream_t);
 
 const void* rod_dirs_kernel() { return (const void*)k_rod_dirs; }
 
@@ -632,9 +472,6 @@ cudaError_t tension_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_newton_solve<double, 32>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(kSolveMaxM * sizeof(double)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_newton_solve_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSolveMaxM * sizeof(float)));
   return e;
 }
 
