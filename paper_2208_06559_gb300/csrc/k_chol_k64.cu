@@ -7,7 +7,7 @@
 // TF32 tensor-core path is not).  Per block column k:
 //   potrf64 : one CTA factors the 64 x 64 diagonal tile and forms its inverse
 //             (the register-blocked routine of the 128-wide path);
-//   trsm64  : L_ik = A_ik W_kk^T, 64 x 64 per CTA, 4 x 4 outputs per thread;
+//   trsm64  : L_ik = A_ik W_kk^T, 64 x 64 per CTA, 8 x 8 outputs per thread;
 //   update64: A_ij -= L_ik L_jk^T for the trailing lower tiles.
 // The 64 x 64 diagonal-tile inverses are kept for the tension solve.
 #include "bd_internal.h"
@@ -31,13 +31,37 @@ __global__ void __launch_bounds__(RegPotrf64::kThreads) k_potrf64(float* __restr
   if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf64::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
 }
 
-// 64 x 64 output tile, 256 threads, 4 x 4 outputs each.
-// TRSM: X = A_ik W_kk^T (overwrites A_ik).  UPDATE: A_ij -= L_ik L_jk^T.
+// 64 x 64 output tile, 64 threads, 8 x 8 outputs each.  The operands (and,
+// for the update, the output tile itself) are copied row-major into shared
+// memory with cp.async, all copies in flight at once.  Thread (i, j) =
+// (t % 8, t / 8) owns rows i + 8a and columns j + 8b (a, b < 8): per four k
+// it reads eight 16-byte row slices of each operand (rows 4 banks apart
+// across a warp: no bank conflicts) for 256 FMAs.  The result is written back
+// from shared memory in coalesced 16-byte rows.
+// TRSM: X = A_ik W_kk^T (overwrites A_ik).  UPDATE: A_ij -= L_ik L_jk^T
+// (diagonal tiles: lower triangle only).
+constexpr int kG64Threads = 64;
+constexpr int kG64P = K64 + 4;  // pitch: 16-byte aligned rows, 4 banks apart
+constexpr int kG64Tile = K64 * kG64P;
+
 template <bool TRSM>
-__global__ void __launch_bounds__(256) k_gemm64(float* __restrict__ K, const float* __restrict__ Kinv,
-                                                const ChainDesc* __restrict__ cd, int k) {
-  __shared__ float X[K64][K64 + 1];
-  __shared__ float Y[K64][K64 + 1];
+constexpr int g64_smem() {
+  return (TRSM ? 2 : 3) * kG64Tile * (int)sizeof(float);
+}
+
+__device__ __forceinline__ void g64_cp16(float* smem, const float* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
+template <bool TRSM>
+__global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, const float* __restrict__ Kinv,
+                                                        const ChainDesc* __restrict__ cd, int k) {
+  extern __shared__ __align__(16) float g64s[];
+  float (*Xs)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s);
+  float (*Ys)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s + kG64Tile);
+  float (*Cs)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s + (TRSM ? 0 : 2 * kG64Tile));
   const ChainDesc d = cd[blockIdx.y];
   const int T = d.mp / K64;
   int i, j;
@@ -60,47 +84,70 @@ __global__ void __launch_bounds__(256) k_gemm64(float* __restrict__ K, const flo
   const float* xs = base + (long long)(i * K64) * mp + k * K64;
   const float* ys = TRSM ? Kinv + (d.kwrow + (long long)k * K64) * K64 : base + (long long)(j * K64) * mp + k * K64;
   const long long ldy = TRSM ? K64 : mp;
-  const int t = threadIdx.x;
-  for (int e = t; e < K64 * K64 / 4; e += 256) {
-    const int r = e >> 4, c4 = (e & 15) * 4;
-    const float4 a = *reinterpret_cast<const float4*>(xs + r * mp + c4);
-    const float4 b = *reinterpret_cast<const float4*>(ys + r * ldy + c4);
-    X[r][c4] = a.x; X[r][c4 + 1] = a.y; X[r][c4 + 2] = a.z; X[r][c4 + 3] = a.w;
-    Y[r][c4] = b.x; Y[r][c4 + 1] = b.y; Y[r][c4 + 2] = b.z; Y[r][c4 + 3] = b.w;
-  }
-  __syncthreads();
-  const int r0 = (t >> 4) * 4, c0 = (t & 15) * 4;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-#pragma unroll 4
-  for (int m = 0; m < K64; ++m) {
-    float xv[4], yv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) xv[a] = X[r0 + a][m];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) yv[b] = Y[c0 + b][m];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += xv[a] * yv[b];
-  }
   float* out = base + (long long)(i * K64) * mp + (TRSM ? k : j) * K64;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < K64 * K64 / 4 / kG64Threads; ++q) {
+    const int e = t + kG64Threads * q;
+    const int r = e >> 4, c4 = (e & 15) * 4;
+    g64_cp16(&Xs[r][c4], xs + r * mp + c4);
+    g64_cp16(&Ys[r][c4], ys + r * ldy + c4);
+    if (!TRSM) g64_cp16(&Cs[r][c4], out + r * mp + c4);
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const int ti = t & 7, tj = t >> 3;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < K64; q += 4) {
+    float4 xv[8], yv[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) xv[a] = *reinterpret_cast<const float4*>(&Xs[ti + 8 * a][q]);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) yv[b] = *reinterpret_cast<const float4*>(&Ys[tj + 8 * b][q]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        float v = acc[a][b];
+        v = fmaf(xv[a].x, yv[b].x, v);
+        v = fmaf(xv[a].y, yv[b].y, v);
+        v = fmaf(xv[a].z, yv[b].z, v);
+        v = fmaf(xv[a].w, yv[b].w, v);
+        acc[a][b] = v;
+      }
+  }
+  if (TRSM) __syncthreads();  // every read of Xs is done: it takes the result
   const bool diag = !TRSM && (i == j);
-  if (TRSM) __syncthreads();  // all reads of A_ik done before it is overwritten (X holds it)
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      float* o = out + (long long)(r0 + a) * mp + c0 + b;
-      if (TRSM) *o = acc[a][b];
-      else if (!diag || c0 + b <= r0 + a) *o -= acc[a][b];
+    for (int b = 0; b < 8; ++b) {
+      const int r = ti + 8 * a, cc = tj + 8 * b;
+      if (TRSM)
+        Cs[r][cc] = acc[a][b];
+      else if (!diag || cc <= r)
+        Cs[r][cc] -= acc[a][b];
     }
+  __syncthreads();
+#pragma unroll 4
+  for (int q = 0; q < K64 * K64 / 4 / kG64Threads; ++q) {
+    const int e = t + kG64Threads * q;
+    const int r = e >> 4, c4 = (e & 15) * 4;
+    *reinterpret_cast<float4*>(out + (long long)r * mp + c4) = *reinterpret_cast<const float4*>(&Cs[r][c4]);
+  }
 }
 
-cudaError_t k64_configure() { return cudaSuccess; }
+cudaError_t k64_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64_smem<false>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64_smem<true>());
+  return e;
+}
 
 bool is_k64_kernel(const void* f) {
   return f == (const void*)k_potrf64 || f == (const void*)k_gemm64<true> || f == (const void*)k_gemm64<false>;
@@ -112,8 +159,9 @@ cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_ch
     k_potrf64<<<n_chains, RegPotrf64::kThreads, 0, s>>>(K, Kinv, cd, k, status);
     const int below = max_tiles - 1 - k;
     if (below > 0) {
-      k_gemm64<true><<<dim3(below, n_chains), 256, 0, s>>>(K, Kinv, cd, k);
-      k_gemm64<false><<<dim3(below * (below + 1) / 2, n_chains), 256, 0, s>>>(K, Kinv, cd, k);
+      k_gemm64<true><<<dim3(below, n_chains), kG64Threads, g64_smem<true>(), s>>>(K, Kinv, cd, k);
+      k_gemm64<false><<<dim3(below * (below + 1) / 2, n_chains), kG64Threads, g64_smem<false>(), s>>>(K, Kinv,
+                                                                                                   cd, k);
     }
   }
   return cudaGetLastError();
