@@ -47,10 +47,11 @@ __device__ __forceinline__ void dfg_add_prod(DFg& a, float g, float th, float tl
 
 // Rows R = pl * mp + k of the three planes; a CTA takes 64 rows of one plane
 // (mp is a multiple of 64).  T (or dT) is split into (hi, lo) floats in
-// shared memory as [column group of 4][hi4, lo4].  Each warp streams its rows
-// with kGvLoads 16-byte loads per lane issued before use; the lane partials
-// are combined with a butterfly (two-sum in double-float mode), after which
-// every lane holds the same sum.
+// shared memory, the high words of all columns first, then the low words
+// (consecutive lanes read consecutive 16-byte words).  Each warp streams its
+// rows with kGvLoads 16-byte loads per lane issued before use; the lane
+// partials are combined with a butterfly (two-sum in double-float mode),
+// after which every lane holds the same sum.
 __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__ G,
                                                        const ChainDesc* __restrict__ cd,
                                                        const double* __restrict__ T,
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__
                                                        double* __restrict__ w,
                                                        const int* __restrict__ state,
                                                        const int* __restrict__ mode) {
-  extern __shared__ __align__(16) float4 tsm[];  // [mp / 4][2]
+  extern __shared__ __align__(16) float4 tsm[];  // [mp / 4] hi words, then [mp / 4] lo words
   const int c = blockIdx.y;
   if (state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
@@ -79,8 +80,8 @@ __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__
       h[q] = (float)v;
       l[q] = (float)(v - (double)h[q]);
     }
-    tsm[2 * e] = make_float4(h[0], h[1], h[2], h[3]);
-    tsm[2 * e + 1] = make_float4(l[0], l[1], l[2], l[3]);
+    tsm[e] = make_float4(h[0], h[1], h[2], h[3]);
+    tsm[mp4 + e] = make_float4(l[0], l[1], l[2], l[3]);
   }
   __syncthreads();
   const int warp = t >> 5, lane = t & 31;
@@ -102,9 +103,9 @@ __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__
       for (int j = 0; j < kGvLoads; ++j) {
         const int q = base + 32 * j + lane;
         if (q >= mp4) break;
-        const float4 th = tsm[2 * q];
+        const float4 th = tsm[q];
         if (df) {
-          const float4 tl = tsm[2 * q + 1];
+          const float4 tl = tsm[mp4 + q];
           dfg_add_prod(acc, g[j].x, th.x, tl.x);
           dfg_add_prod(acc, g[j].y, th.y, tl.y);
           dfg_add_prod(acc, g[j].z, th.z, tl.z);

@@ -258,10 +258,12 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
 
 // K for the mixed path straight from the positions, so that it needs neither
 // D nor the assembly and runs beside it: per 32 x 32 rod tile (kt >= lt) the
-// RPY coefficients of the 33 x 33 bead pairs the tile touches (Eqs. (8)-(9),
-// FP32 from positions split into float pairs) are formed once in shared
-// memory, then with B_kl = D_k,l - D_k,l+1 - D_k+1,l + D_k+1,l+1 (= B_lk,
-// a symmetric 3 x 3 block; D_aa = I)
+// 3 x 3 blocks D_xy = cI I + cRR R R^T of the 33 x 33 bead pairs the tile
+// touches (Eqs. (8)-(9), FP32 from positions split into float pairs; D_aa =
+// I) are formed once in shared memory as their six distinct entries; then
+// per rod pair the second difference
+//   B_kl = D_k,l - D_k,l+1 - D_k+1,l + D_k+1,l+1   (symmetric 3 x 3, = B_lk)
+// gives
 //   G_kl = B_kl u_l,  G_lk = B_kl u_k  (the rod-space mobility C D C^T U,
 //                                        three planes [3][mp][mp], optional)
 //   K_kl = u_k . G_kl  (lower triangle).
@@ -274,8 +276,7 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
                                                     float* __restrict__ G,
                                                     const ChainDesc* __restrict__ cd,
                                                     const double* __restrict__ uhat, float hstar, float arad) {
-  __shared__ float cI[KB][KB + 1], cRR[KB][KB + 1];
-  __shared__ float Rv[3][KB][KB + 1];
+  __shared__ float Ds[6][KB][KB];  // xx, xy, xz, yy, yz, zz of D_xy
   __shared__ float ph[2][KB][3], pl[2][KB][3];  // split positions: [0] k side, [1] l side
   __shared__ float uk[KR][3], ul[KR][3];
   __shared__ float St[3][KR][KR + 1];            // G_lk staged for a coalesced transposed store
@@ -309,20 +310,27 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
   for (int e = t; e < KB * KB; e += blockDim.x) {
     const int x = e / KB, y = e % KB;
     const int a = KR * kt + x, b = KR * lt + y;
-    float ci = 0.0f, cr = 0.0f, R[3] = {0.0f, 0.0f, 0.0f};
+    float dv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (a < N && b < N) {
       if (a == b) {
-        ci = 1.0f;
+        dv[0] = dv[3] = dv[5] = 1.0f;
       } else {
+        float R[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) R[q] = (ph[0][x][q] - ph[1][y][q]) + (pl[0][x][q] - pl[1][y][q]);
+        float ci, cr;
         rpy_coeffs<float>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, arad, ci, cr);
+        const float c0 = cr * R[0], c1 = cr * R[1];
+        dv[0] = fmaf(c0, R[0], ci);
+        dv[1] = c0 * R[1];
+        dv[2] = c0 * R[2];
+        dv[3] = fmaf(c1, R[1], ci);
+        dv[4] = c1 * R[2];
+        dv[5] = fmaf(cr * R[2], R[2], ci);
       }
     }
-    cI[x][y] = ci;
-    cRR[x][y] = cr;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) Rv[q][x][y] = R[q];
+    for (int q = 0; q < 6; ++q) Ds[q][x][y] = dv[q];
   }
   __syncthreads();
   const long long mp = d.mp;
@@ -331,25 +339,14 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
     const int ia = e / KR, ib = e % KR;  // rod k = 32 kt + ia, rod l = 32 lt + ib
     const int k = KR * kt + ia, l = KR * lt + ib;
     const bool valid = k < m && l < m && l <= k;
+    float B[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      B[q] = (Ds[q][ia][ib] - Ds[q][ia][ib + 1]) + (Ds[q][ia + 1][ib + 1] - Ds[q][ia + 1][ib]);
     const float u0 = uk[ia][0], u1 = uk[ia][1], u2 = uk[ia][2];
     const float v0 = ul[ib][0], v1 = ul[ib][1], v2 = ul[ib][2];
-    float bv[3] = {0.0f, 0.0f, 0.0f}, bu[3] = {0.0f, 0.0f, 0.0f};  // B u_l, B u_k
-#pragma unroll
-    for (int da = 0; da < 2; ++da)
-#pragma unroll
-      for (int db = 0; db < 2; ++db) {
-        const int x = ia + da, y = ib + db;
-        const float sg = (da == db) ? 1.0f : -1.0f;
-        const float R0 = Rv[0][x][y], R1 = Rv[1][x][y], R2 = Rv[2][x][y];
-        const float ci = sg * cI[x][y], cr = sg * cRR[x][y];
-        const float Rv_ = cr * (R0 * v0 + R1 * v1 + R2 * v2), Ru = cr * (R0 * u0 + R1 * u1 + R2 * u2);
-        bv[0] += ci * v0 + Rv_ * R0;
-        bv[1] += ci * v1 + Rv_ * R1;
-        bv[2] += ci * v2 + Rv_ * R2;
-        bu[0] += ci * u0 + Ru * R0;
-        bu[1] += ci * u1 + Ru * R1;
-        bu[2] += ci * u2 + Ru * R2;
-      }
+    const float bv[3] = {B[0] * v0 + B[1] * v1 + B[2] * v2, B[1] * v0 + B[3] * v1 + B[4] * v2,
+                         B[2] * v0 + B[4] * v1 + B[5] * v2};  // B u_l
     if (valid) {
       K[d.koff + (long long)k * mp + l] = u0 * bv[0] + u1 * bv[1] + u2 * bv[2];
       if (Gc) {
@@ -358,8 +355,10 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
       }
     }
     if (Gc) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) St[q][ia][ib] = (valid && l < k) ? bu[q] : 0.0f;
+      const bool lower = valid && l < k;
+      St[0][ia][ib] = lower ? B[0] * u0 + B[1] * u1 + B[2] * u2 : 0.0f;  // B u_k
+      St[1][ia][ib] = lower ? B[1] * u0 + B[3] * u1 + B[4] * u2 : 0.0f;
+      St[2][ia][ib] = lower ? B[2] * u0 + B[4] * u1 + B[5] * u2 : 0.0f;
     }
   }
   if (!Gc) return;
