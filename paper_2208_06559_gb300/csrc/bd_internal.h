@@ -137,7 +137,7 @@ cudaError_t launch_tension_products_g(const float* G, const ChainDesc* cd, int n
 cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const ChainDesc* cd,
                                      int n_chains, Phys ph, double* rhs, int* state, int* status,
                                      const int* iters, int* mode, cudaStream_t s);
-cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const double* rstar,
+cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const float* M, const double* rstar,
                               const double* w, const double* F, double* r, const int* state, int* status,
                               StepArgs* args, cudaStream_t s);
 cudaError_t gmode_configure();

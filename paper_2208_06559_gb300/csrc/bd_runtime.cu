@@ -247,8 +247,8 @@ int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
 // the rods), step index advanced.
 int enqueue_finalize(bd_ctx* c, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_finalize_g(c->d_cd, c->n_chains, c->ph, c->rstar, c->u, c->F, c->r, c->state, c->status,
-                         c->args, s));
+    CK(launch_finalize_g(c->d_cd, c->n_chains, c->ph, (const float*)c->M, c->rstar, c->u, c->F, c->r, c->state,
+                         c->status, c->args, s));
   else
     CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status, c->args,
                        s));

@@ -19,7 +19,6 @@
 //   k_finalize_g     : positions of converged chains from the rods.
 #include "bd_internal.h"
 #include "block_dev.h"
-#include "rpy_dev.h"
 
 namespace bd {
 
@@ -203,13 +202,15 @@ __global__ void __launch_bounds__(256) k_newton_residual_g(const double* __restr
 }
 
 // One CTA (1024 threads) per chain, converged chains only: bead 0 moves by
-// dt (D F)_0 (D_0j from the positions at the start of the step, Eqs. (7)-(9),
-// D_00 = I) and the rods Q_k = Q*_k - dt w_k are summed from it.  Failed
-// chains keep their positions; the step index advances as in k_finalize.
+// dt (D F)_0 (D_0j, Eqs. (7)-(9), read from rows 0-2 of the stored FP32
+// mobility matrix, whose upper triangle still holds D; D_00 = I) and the
+// rods Q_k = Q*_k - dt w_k are summed from it.  Failed chains keep their
+// positions; the step index advances as in k_finalize.
 constexpr int kFinThreads = 1024;
 constexpr int kFinPer = 4;  // beads per thread (N <= 4096)
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __restrict__ cd, Phys ph,
+                                                            const float* __restrict__ M,
                                                             const double* __restrict__ rstar,
                                                             const double* __restrict__ w,
                                                             const double* __restrict__ F,
@@ -231,9 +232,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __r
   double* rc = r + 3 * d.boff;
   const double* rs = rstar + 3 * d.boff;
   const double* Fc = F + 3 * d.boff;
-  // (D F)_0 from the old positions
+  // (D F)_0 from row block 0 of D
   double df[3] = {0.0, 0.0, 0.0};
-  const double r00 = rc[0], r01 = rc[1], r02 = rc[2];
+  const float* M0 = M + d.moff;
+  const long long np = d.np;
   for (int j = t; j < N; j += kFinThreads) {
     const double f0 = Fc[3 * j], f1 = Fc[3 * j + 1], f2 = Fc[3 * j + 2];
     if (j == 0) {
@@ -241,16 +243,14 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __r
       df[1] += f1;
       df[2] += f2;
     } else {
-      const double R0 = r00 - rc[3 * j], R1 = r01 - rc[3 * j + 1], R2 = r02 - rc[3 * j + 2];
-      double ci, cr;
-      rpy_coeffs<double>(R0 * R0 + R1 * R1 + R2 * R2, ph.hstar, ph.a, ci, cr);
-      const double rf = cr * (R0 * f0 + R1 * f1 + R2 * f2);
-      df[0] += ci * f0 + rf * R0;
-      df[1] += ci * f1 + rf * R1;
-      df[2] += ci * f2 + rf * R2;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float* row = M0 + q * np + 3 * j;
+        df[q] += (double)row[0] * f0 + (double)row[1] * f1 + (double)row[2] * f2;
+      }
     }
   }
-  block_sum3(df, red);  // ends with a barrier: every read of the old positions is done
+  block_sum3(df, red);
   // rods of this thread's beads i0 .. i0 + 3 (rod k joins bead k to k + 1)
   const int i0 = kFinPer * t;
   double q[kFinPer][3], off[3] = {0.0, 0.0, 0.0};
@@ -292,10 +292,10 @@ cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const double* rstar,
+cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const float* M, const double* rstar,
                               const double* w, const double* F, double* r, const int* state, int* status,
                               StepArgs* args, cudaStream_t s) {
-  k_finalize_g<<<n_chains, kFinThreads, 0, s>>>(cd, ph, rstar, w, F, r, state, status, args);
+  k_finalize_g<<<n_chains, kFinThreads, 0, s>>>(cd, ph, M, rstar, w, F, r, state, status, args);
   return cudaGetLastError();
 }
 

@@ -180,3 +180,58 @@ def test_profiled_step_equals_graph_step(bd):
         out.append(ctx.get_state().cpu().numpy())
         ctx.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+# Rod counts m = N - 1 at the edges of the tension path's blocking: the
+# 64-wide tiles of K's factor (m = 64, 65), the 256-wide super-blocks of the
+# solve (m = 255, 256, 257, 512) and a ragged multi-super-block chain.
+EDGE_SIZES = [2, 65, 66, 256, 257, 258, 513, 1300]
+
+
+def test_rod_space_iteration_without_hi_matches_fp64(bd):
+    """h* = 0 makes D = I exactly, so the mixed and FP64 paths share the
+    Brownian displacement and differ only in the tension iteration (rod
+    space, FP32 G with FP32-rounded directions, super-block solve) against
+    the FP64 bead-space iteration: after 3 steps of shear the positions agree
+    to ~1e-8 of the displacement."""
+    Nc = np.array(EDGE_SIZES, np.int32)
+    r0 = inputs.random_walk(Nc, 51)
+    noise = cuda(inputs.gaussian_noise(3, int(Nc.sum()), 52))
+    out = {}
+    for prec in (bd.FP64, bd.MIXED_TF32):
+        ctx = bd.Context(Nc, precision=prec, flow=1, Wi=100.0, h_star=0.0)
+        ctx.set_state(cuda(r0))
+        ctx.step(noise)
+        obs, st = ctx.observables()
+        assert (st == 0).all(), (prec, st)
+        assert obs[:, bd.OBS_MAXDEV].max().item() < 1e-10
+        out[prec] = ctx.get_state().cpu().numpy()
+        ctx.close()
+    d64 = out[bd.FP64] - r0
+    err = np.abs(out[bd.MIXED_TF32] - out[bd.FP64]).max() / np.abs(d64).max()
+    assert err < 1e-6, err
+
+
+def test_rod_space_iteration_edge_sizes_with_hi(bd):
+    """With hydrodynamic interactions at the same edge sizes: every chain
+    converges within the FP64 path's iteration count + 2, rods hold to
+    1e-10, and the displacement stays within the TF32 factor's reach of the
+    FP64 path."""
+    Nc = np.array(EDGE_SIZES, np.int32)
+    r0 = inputs.random_walk(Nc, 53)
+    noise = cuda(inputs.gaussian_noise(2, int(Nc.sum()), 54))
+    out, its = {}, {}
+    for prec in (bd.FP64, bd.MIXED_TF32):
+        ctx = bd.Context(Nc, precision=prec, flow=1, Wi=100.0)
+        ctx.set_state(cuda(r0))
+        ctx.step(noise)
+        obs, st = ctx.observables()
+        assert (st == 0).all(), (prec, st)
+        assert obs[:, bd.OBS_MAXDEV].max().item() < 1e-10
+        its[prec] = obs[:, bd.OBS_NEWTON].cpu().numpy()
+        out[prec] = ctx.get_state().cpu().numpy()
+        ctx.close()
+    assert (its[bd.MIXED_TF32] <= its[bd.FP64] + 2).all(), its
+    d64 = out[bd.FP64] - r0
+    err = np.abs(out[bd.MIXED_TF32] - out[bd.FP64]).max() / np.abs(d64).max()
+    assert err < 5e-2, err
