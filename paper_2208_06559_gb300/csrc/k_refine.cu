@@ -97,110 +97,30 @@ __global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
   }
 }
 
-// z = Lt^{-T} x: one CTA (1024 threads) per chain, 128-row blocks from the
-// last to the first.  Thread t owns columns a = t, t + 1024, ...; after block
-// b is solved (z_b = W_bb^T (x_b - acc_b), W_bb the stored inverse of the
+// z = Lt^{-T} x, 128-row blocks from the last to the first: after block b
+// is solved (z_b = W_bb^T (x_b - acc_b), W_bb the stored inverse of the
 // diagonal tile, staged in shared memory and applied by all 1024 threads,
-// eight partial sums per output) every thread adds sum_{rho in b} Lt[rho][a]
-// z_rho to its columns a < 128 b: each row of Lt is read once, coalesced.
+// eight partial sums per output) every owned column a < 128 b gets
+// sum_{rho in b} Lt[rho][a] z_rho: each row of Lt is read once, coalesced.
 constexpr int kTrsvThreads = 1024;
 constexpr int kTrsvMaxCols = 12;  // np <= 12288 (N <= 4096)
-constexpr int kTrsvSmem = (kMixedTile * kMixedTile + 2 * 8 * kMixedTile) * 4;  // W_b, partials
+constexpr int kTrsvW = kMixedTile * kMixedTile;
+constexpr int kTrsvSmem = (2 * kTrsvW + 2 * 8 * kMixedTile) * 4;  // W_b double buffer, partials
 
-__global__ void __launch_bounds__(kTrsvThreads) k_trsv_t_f32(const float* __restrict__ M,
-                                                             const float* __restrict__ Winv,
-                                                             const ChainDesc* __restrict__ cd,
-                                                             const double* __restrict__ x_in,
-                                                             const StepArgs* __restrict__ args,
-                                                             double* __restrict__ z) {
-  extern __shared__ __align__(16) float tv_smem[];
-  float* Ws = tv_smem;                                  // [128][128] W_bb
-  float* ph = Ws + kMixedTile * kMixedTile;             // [8][128] partial hi
-  float* pl = ph + 8 * kMixedTile;                      // [8][128] partial lo
-  __shared__ double sacc[128];
-  __shared__ float zh[128], zl[128], sh[128], sl[128];
-  const ChainDesc d = cd[blockIdx.x];
-  const int T = d.np / kMixedTile;
-  const double* x = args ? args->noise + (long long)args->step * args->stride : x_in;
-  x += 3 * d.boff;
-  const float* base = M + d.moff;
-  const long long np = d.np;
-  const int t = threadIdx.x;
-  DFa acc[kTrsvMaxCols];
-#pragma unroll
-  for (int q = 0; q < kTrsvMaxCols; ++q) acc[q] = DFa{0.f, 0.f};
-  for (int b = T - 1; b >= 0; --b) {
-    const int c0 = 128 * b;
-    {  // stage W_bb (16 KB rows, coalesced float4)
-      const float4* Wg = reinterpret_cast<const float4*>(Winv + ((long long)d.wrow + c0) * kMixedTile);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(Ws)[t + kTrsvThreads * q] = __ldg(Wg + t + kTrsvThreads * q);
-    }
-    // columns of block b owned by this thread: a = t + 1024 q in [c0, c0 + 128)
-#pragma unroll
-    for (int q = 0; q < kTrsvMaxCols; ++q) {
-      const int a = t + kTrsvThreads * q;
-      if (a >= c0 && a < c0 + 128) sacc[a - c0] = (double)acc[q].hi + (double)acc[q].lo;
-    }
-    __syncthreads();
-    if (t < 128) {
-      const int a = c0 + t;
-      const double rhs = ((a < d.n) ? x[a] : 0.0) - sacc[t];
-      sh[t] = (float)rhs;
-      sl[t] = (float)(rhs - (double)sh[t]);
-    }
-    __syncthreads();
-    {  // z_i = sum_{j >= i} W[j][i] s_j: output i = t % 128, rows j in [16 p, 16 p + 16)
-      const int i = t & 127, p = t >> 7;
-      DFa zi{0.f, 0.f};
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const int j = 16 * p + jj;
-        if (j >= i) dfa_add_prod(zi, Ws[j * kMixedTile + i], sh[j], sl[j]);
-      }
-      ph[p * kMixedTile + i] = zi.hi;
-      pl[p * kMixedTile + i] = zi.lo;
-    }
-    __syncthreads();
-    if (t < 128) {
-      DFa zi{ph[t], pl[t]};
-#pragma unroll
-      for (int p = 1; p < 8; ++p) dfa_add(zi, ph[p * kMixedTile + t], pl[p * kMixedTile + t]);
-      const double v = (double)zi.hi + (double)zi.lo;
-      zh[t] = (float)v;
-      zl[t] = (float)(v - (double)zh[t]);
-      if (c0 + t < d.n) z[3 * d.boff + c0 + t] = v;
-    }
-    __syncthreads();
-    if (b == 0) break;
-    // contributions of block b to every column a < c0
-#pragma unroll
-    for (int q = 0; q < kTrsvMaxCols; ++q) {
-      const int a = t + kTrsvThreads * q;
-      if (a < c0) {
-        const float* col = base + (long long)c0 * np + a;
-        DFa s = acc[q];
-        // 16 independent loads in flight before the dependent accumulation
-        for (int r0 = 0; r0 < 128; r0 += 16) {
-          float v[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = __ldg(col + (long long)(r0 + j) * np);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) dfa_add_prod(s, v[j], zh[r0 + j], zl[r0 + j]);
-        }
-        acc[q] = s;
-      }
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void trsv_cp16(float* smem, const float* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
 }
 
-// The same solve split over a cluster of two CTAs per chain: CTA `rank` owns
+// The solve is split over a cluster of two CTAs per chain: CTA `rank` owns
 // the columns of the 128-wide blocks B with B % 2 == rank (local column
 // l = t + 1024 q -> block 2 (l / 128) + rank).  For block b the owner
 // publishes its 128 accumulated sums through distributed shared memory,
 // both CTAs form z_b (the same arithmetic, so identical copies), and each
-// adds block b's contributions to the columns it owns.  Rank 0 writes z.
+// adds block b's contributions to the columns it owns.  W_{b-1} is copied
+// (cp.async) into the other half of a double buffer while block b is
+// processed.  Rank 0 writes z.
 constexpr int kTrsvColsCl = 6;  // owned columns per thread: np <= 12288
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
@@ -210,8 +130,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   extern __shared__ __align__(16) float tv_smem[];
-  float* Ws = tv_smem;                       // [128][128] W_bb
-  float* ph = Ws + kMixedTile * kMixedTile;  // [8][128] partial hi
+  float* Wbuf = tv_smem;                     // [2][128][128] W_bb, double buffered
+  float* ph = Wbuf + 2 * kTrsvW;             // [8][128] partial hi
   float* pl = ph + 8 * kMixedTile;           // [8][128] partial lo
   __shared__ float pub_h[2][128], pub_l[2][128];  // published sums of an owned block (by parity)
   __shared__ float zh[128], zl[128], sh[128], sl[128];
@@ -229,14 +149,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
     const int l = t + kTrsvThreads * q;
     return kMixedTile * (2 * (l >> 7) + rank) + (l & 127);
   };
+  auto stage_w = [&](int b, float* dst) {  // W_bb -> dst, 16 KB per quarter, one group
+    const float* Wg = Winv + ((long long)d.wrow + kMixedTile * b) * kMixedTile;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) trsv_cp16(dst + 4 * (t + kTrsvThreads * q), Wg + 4 * (t + kTrsvThreads * q));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  stage_w(T - 1, Wbuf);
   int par = 0;
   for (int b = T - 1; b >= 0; --b, par ^= 1) {
     const int c0 = 128 * b;
-    {  // stage W_bb
-      const float4* Wg = reinterpret_cast<const float4*>(Winv + ((long long)d.wrow + c0) * kMixedTile);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(Ws)[t + kTrsvThreads * q] = __ldg(Wg + t + kTrsvThreads * q);
-    }
+    float* Ws = Wbuf + par * kTrsvW;
+    if (b > 0) stage_w(b - 1, Wbuf + (par ^ 1) * kTrsvW);
     if ((b & 1) == rank) {  // publish the sums of block b's columns
 #pragma unroll
       for (int q = 0; q < kTrsvColsCl; ++q) {
@@ -257,6 +181,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
       sh[t] = (float)rhs;
       sl[t] = (float)(rhs - (double)sh[t]);
     }
+    if (b > 0)  // W_bb landed; W_{b-1} may still be in flight
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     {  // z_i = sum_{j >= i} W[j][i] s_j: output i = t % 128, rows j in [16 p, 16 p + 16)
       const int i = t & 127, p = t >> 7;
@@ -354,10 +282,7 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
 }
 
 cudaError_t refine_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_trsv_t_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_trsv_t_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
-  return e;
+  return cudaFuncSetAttribute(k_trsv_t_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
 }
 
 }  // namespace bd
