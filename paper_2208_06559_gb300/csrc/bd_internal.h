@@ -170,7 +170,6 @@ cudaError_t launch_fraenkel_update(double* r, const double* y, const double* u, 
 cudaError_t launch_step_done(StepArgs* args, cudaStream_t s);
 // Kernels of the rod-coupling-matrix chain (K formation and factorisation),
 // for per-node priorities in the captured step graph.
-const void* form_k_kernel(bool fp32);
 const void* form_k_pos_kernel();
 bool is_k64_kernel(const void* f);
 const void* rod_dirs_kernel();

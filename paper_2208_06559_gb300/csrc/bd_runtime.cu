@@ -290,7 +290,7 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
     if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
-    const bool kchain = c->mixed && (kp.func == form_k_kernel(true) || kp.func == rod_dirs_kernel() ||
+    const bool kchain = c->mixed && (kp.func == rod_dirs_kernel() ||
                                      is_k64_kernel(kp.func) || kp.func == form_k_pos_kernel() ||
                                      is_sb_inverse_kernel(kp.func));
     cudaLaunchAttributeValue v;

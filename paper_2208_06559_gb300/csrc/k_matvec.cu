@@ -152,7 +152,8 @@ cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_n
 }
 
 // ---------------------------------------------------------------- form_k
-// K_kl = u_k^T (D_kl - D_k,l+1 - D_k+1,l + D_k+1,l+1) u_l for rods k >= l.
+// FP64 path: K_kl = u_k^T (D_kl - D_k,l+1 - D_k+1,l + D_k+1,l+1) u_l for rods
+// k >= l (the mixed path forms K from the positions, k_form_k_pos).
 // CTA per 32 x 32 rod tile (kt >= lt): the 99 x 99 element region of D that
 // the tile needs (beads 32 lt .. 32 lt + 32 against 32 kt .. 32 kt + 32) is
 // staged in shared memory from the strict upper triangle with coalesced row
@@ -165,9 +166,7 @@ constexpr int form_k_smem() {
   return (int)(KE * (KE + 1) * sizeof(T) + 2 * KR * 3 * sizeof(T));
 }
 
-// Arithmetic in the storage type T: K only serves as the Jacobian of the
-// tension iteration (it fixes the convergence rate, not the root), so FP32
-// is enough for the mixed path.
+// Arithmetic in the storage type T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __restrict__ K,
                                                 const ChainDesc* __restrict__ cd,
@@ -397,8 +396,6 @@ template cudaError_t launch_symv<double>(const double*, const ChainDesc*, int, i
                                          double*, double*, const int*, cudaStream_t);
 template cudaError_t launch_form_k<double>(const double*, double*, const ChainDesc*, int, int,
                                            const double*, cudaStream_t);
-template cudaError_t launch_form_k<float>(const float*, float*, const ChainDesc*, int, int,
-                                          const double*, cudaStream_t);
 
 }  // namespace bd
 
@@ -630,17 +627,9 @@ cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, i
 
 const void* form_k_pos_kernel() { return (const void*)k_form_k_pos; }
 
-const void* form_k_kernel(bool fp32) {
-  return fp32 ? (const void*)k_form_k<float> : (const void*)k_form_k<double>;
-}
-
 cudaError_t matvec_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_form_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             form_k_smem<float>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_form_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             form_k_smem<double>());
-  return e;
+  return cudaFuncSetAttribute(k_form_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              form_k_smem<double>());
 }
 
 }  // namespace bd

@@ -235,3 +235,27 @@ def test_rod_space_iteration_edge_sizes_with_hi(bd):
     d64 = out[bd.FP64] - r0
     err = np.abs(out[bd.MIXED_TF32] - out[bd.FP64]).max() / np.abs(d64).max()
     assert err < 5e-2, err
+
+
+def test_step_brownian_displacement_matches_stage_api(bd):
+    """The Brownian displacement inside a graph-replayed step (several chain
+    groups, ragged lengths) is the one the stage API computes.  In
+    the Fraenkel mode with dt = 1e-12 the link update leaves the explicit step
+    unchanged up to 2 dt K* ~ 2e-8 of the link stretch, and the unit bonds of
+    the start carry no spring force, so r1 - r0 must equal the standalone
+    displacement of the same factor (bd_assemble, bd_factor, bd_brownian)."""
+    Nc = np.array([300, 40, 129, 300, 86, 300, 2, 213] * 5, np.int32)
+    r0 = inputs.random_walk(Nc, 61)
+    xi = inputs.gaussian_noise(1, int(Nc.sum()), 62)
+    ctx = bd.Context(Nc, precision=bd.MIXED_TF32, dt=1e-12, constraint=bd.FRAENKEL, k_spring=1e4)
+    ctx.set_state(cuda(r0))
+    ctx.assemble()
+    ctx.factor()
+    y = ctx.brownian(cuda(xi[0])).cpu().numpy()
+    ctx.step(cuda(xi))
+    _, st = ctx.observables()
+    assert (st == 0).all(), st
+    dr = ctx.get_state().cpu().numpy() - r0
+    err = np.abs(dr - y).max() / np.abs(y).max()
+    assert err < 1e-6, err
+    ctx.close()
