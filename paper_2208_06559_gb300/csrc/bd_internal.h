@@ -92,8 +92,10 @@ cudaError_t launch_symv(const T* M, const ChainDesc* cd, int n_chains, int max_n
 // iteration (k_gmode.cu): the full product w = G T or the increment
 // w += G dT, in plain FP32 or in compensated (double-float) FP32.
 enum MobMode : int { MOB_FULL_F32 = 0, MOB_FULL_DF = 1, MOB_INC_DF = 2, MOB_INC_F32 = 3 };
-// FP32-storage mobility product u = D f to FP64-level accuracy (double-float
-// sums).  fsplit: [sum np] float2; scratch: the two-phase partials.
+// FP32-storage mobility product u = D f with FP32 arithmetic: groups of four
+// products summed in FP32, the group sums added with a two-sum (relative
+// error a few FP32 round-offs, independent of the length of the sum).
+// fsplit: [sum np] float2; scratch: the two-phase partials.
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
                             const double* f, float2* fsplit, double* scratch, double* u,
                             const int* state, cudaStream_t s);

@@ -402,15 +402,17 @@ template cudaError_t launch_form_k<double>(const double*, double*, const ChainDe
 namespace bd {
 
 // ---------------------------------------------------- symv, FP32 storage
-// u = D f for D stored in FP32, to FP64-level accuracy with FP32 arithmetic
-// only (the FP64 pipe of this part runs at 1/64 of the FP32 rate):
+// u = D f for D stored in FP32 with FP32 arithmetic only (the FP64 pipe of
+// this part runs at 1/64 of the FP32 rate), to a relative error of a few
+// FP32 unit round-offs of the result, with no growth in the length of the sum:
 //   k_split_f2      : f (FP64) -> (fh, fl) float pairs once per product,
 //                     zero-padded to the chain's padded order;
-//   k_symv_tiles_f32: per 64 x 64 tile of the upper triangle, every product
-//                     d*fh is made exact with an FMA (p + e), the p terms are
-//                     summed with a compensated (two-sum) accumulator and the
-//                     small terms in a plain float; row sums and column sums
-//                     of the tile go out as (hi, lo) pairs;
+//   k_symv_tiles_f32: per 64 x 64 tile of the upper triangle, groups of four
+//                     products d*fh are summed in FP32 (three roundings of
+//                     the group sum) and each group sum is added to a
+//                     compensated (two-sum) accumulator; the d*fl terms go to
+//                     a plain float beside it; row sums and column sums of
+//                     the tile go out as (hi, lo) pairs;
 //   k_symv_reduce_df: per row, compensated sum of its tile partials, one
 //                     conversion to FP64.
 // A tile is staged in shared memory (128 threads: thread t < 64 sums row t,
@@ -426,14 +428,17 @@ struct DF {
   float hi, lo;
 };
 
-__device__ __forceinline__ void df_add_prod(DF& a, float d, float fh, float fl) {
-  const float p = d * fh;
-  const float e = fmaf(d, fh, -p);  // exact: d * fh = p + e
+// a += d0 f0 + d1 f1 + d2 f2 + d3 f3, f = (h0, l0, h1, l1), (h2, l2, h3, l3):
+// the high products summed in FP32, the sum added to a with a two-sum, the
+// low products accumulated in `lo` (folded into a.lo at the end).
+__device__ __forceinline__ void df_add4(DF& a, float& lo, float d0, float d1, float d2, float d3, float4 f01,
+                                        float4 f23) {
+  const float p = fmaf(d3, f23.z, fmaf(d2, f23.x, fmaf(d1, f01.z, d0 * f01.x)));
+  lo = fmaf(d3, f23.w, fmaf(d2, f23.y, fmaf(d1, f01.w, fmaf(d0, f01.y, lo))));
   const float s = a.hi + p;
   const float bp = s - a.hi;
-  const float err = (a.hi - (s - bp)) + (p - bp);
+  a.lo += (a.hi - (s - bp)) + (p - bp);
   a.hi = s;
-  a.lo += err + e + d * fl;
 }
 
 // (bj, bi), bi <= bj, of upper-triangle tile p (column-major enumeration),
@@ -547,28 +552,21 @@ __global__ void __launch_bounds__(128) k_symv_tiles_f32(const float* __restrict_
       {
         if (t < SF) {
           DF acc{0.f, 0.f};
+          float lo = 0.f;
 #pragma unroll 4
           for (int q4 = 0; q4 < SF / 4; ++q4) {
             const float4 v = *reinterpret_cast<const float4*>(&Sb[t][4 * q4]);
-            const float4 f01 = fc4[2 * q4], f23 = fc4[2 * q4 + 1];
-            df_add_prod(acc, v.x, f01.x, f01.y);
-            df_add_prod(acc, v.y, f01.z, f01.w);
-            df_add_prod(acc, v.z, f23.x, f23.y);
-            df_add_prod(acc, v.w, f23.z, f23.w);
+            df_add4(acc, lo, v.x, v.y, v.z, v.w, fc4[2 * q4], fc4[2 * q4 + 1]);
           }
-          Pc[bj * ld + r0 + t] = make_float2(acc.hi, acc.lo);  // rows of bi from column block bj
+          Pc[bj * ld + r0 + t] = make_float2(acc.hi, acc.lo + lo);  // rows of bi from column block bj
         } else if (!diag) {
           const int q = t - SF;
           DF acc{0.f, 0.f};
+          float lo = 0.f;
 #pragma unroll 4
-          for (int r = 0; r < SF; r += 4) {
-            const float4 f01 = fr4[r >> 1], f23 = fr4[(r >> 1) + 1];
-            df_add_prod(acc, Sb[r][q], f01.x, f01.y);
-            df_add_prod(acc, Sb[r + 1][q], f01.z, f01.w);
-            df_add_prod(acc, Sb[r + 2][q], f23.x, f23.y);
-            df_add_prod(acc, Sb[r + 3][q], f23.z, f23.w);
-          }
-          Pc[bi * ld + c0 + q] = make_float2(acc.hi, acc.lo);  // rows of bj from column block bi
+          for (int r = 0; r < SF; r += 4)
+            df_add4(acc, lo, Sb[r][q], Sb[r + 1][q], Sb[r + 2][q], Sb[r + 3][q], fr4[r >> 1], fr4[(r >> 1) + 1]);
+          Pc[bi * ld + c0 + q] = make_float2(acc.hi, acc.lo + lo);  // rows of bj from column block bi
         }
       }
     }

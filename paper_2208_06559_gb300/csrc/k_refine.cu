@@ -9,10 +9,13 @@
 // (D' = Lt Lt^T): the error drops from first to second order in E, with the
 // same xi, so the path stays comparable with the FP64 factor.
 //
-// All three products read FP32 matrices and accumulate in compensated FP32
-// (double-float): each xi or z value is split into two floats, each product
-// d * hi is made exact with an FMA and summed with two-sum, so the results
-// carry FP64-level accuracy without FP64 arithmetic (slow on this part).
+// All three products read FP32 matrices and accumulate in compensated FP32:
+// each xi or z value is split into two floats; the triangular solve makes
+// every product d * hi exact with an FMA and sums with two-sum (double-float,
+// FP64-level), the two products by Lt and D sum groups of four products in
+// FP32 before the two-sum (a few FP32 round-offs of the result, far below
+// the refinement's second-order factor error) -- no FP64 arithmetic, which is
+// slow on this part.
 #include <cooperative_groups.h>
 
 #include "bd_internal.h"
@@ -38,6 +41,19 @@ __device__ __forceinline__ void dfa_add(DFa& a, float bh, float bl) {
   const float s = a.hi + bh;
   const float bp = s - a.hi;
   a.lo += ((a.hi - (s - bp)) + (bh - bp)) + bl;
+  a.hi = s;
+}
+
+// a += d0 x0 + d1 x1 + d2 x2 + d3 x3 with x = xh + xl: the high products
+// summed in FP32 and added with a two-sum, the low ones into `lo`.
+__device__ __forceinline__ void dfa_add4(DFa& a, float& lo, float d0, float d1, float d2, float d3, float h0,
+                                         float h1, float h2, float h3, float l0, float l1, float l2,
+                                         float l3) {
+  const float p = fmaf(d3, h3, fmaf(d2, h2, fmaf(d1, h1, d0 * h0)));
+  lo = fmaf(d3, l3, fmaf(d2, l2, fmaf(d1, l1, fmaf(d0, l0, lo))));
+  const float s = a.hi + p;
+  const float bp = s - a.hi;
+  a.lo += (a.hi - (s - bp)) + (p - bp);
   a.hi = s;
 }
 
@@ -82,16 +98,16 @@ __global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
     if (row >= d.n) return;
     const float* Lr = base + (long long)row * d.np;
     DFa acc{0.f, 0.f};
+    float lo = 0.f;
     int c = lane;
     for (; c + 96 <= row; c += 128) {  // four loads in flight per lane
       const float v0 = __ldg(Lr + c), v1 = __ldg(Lr + c + 32), v2 = __ldg(Lr + c + 64),
                   v3 = __ldg(Lr + c + 96);
-      dfa_add_prod(acc, v0, xh[c], xl[c]);
-      dfa_add_prod(acc, v1, xh[c + 32], xl[c + 32]);
-      dfa_add_prod(acc, v2, xh[c + 64], xl[c + 64]);
-      dfa_add_prod(acc, v3, xh[c + 96], xl[c + 96]);
+      dfa_add4(acc, lo, v0, v1, v2, v3, xh[c], xh[c + 32], xh[c + 64], xh[c + 96], xl[c], xl[c + 32],
+               xl[c + 64], xl[c + 96]);
     }
     for (; c <= row; c += 32) dfa_add_prod(acc, Lr[c], xh[c], xl[c]);
+    acc.lo += lo;
     acc = dfa_warp_sum(acc);
     if (lane == 0) y[3 * d.boff + row] = scale * ((double)acc.hi + (double)acc.lo);
   }

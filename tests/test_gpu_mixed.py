@@ -114,17 +114,27 @@ def test_refined_brownian_displacement(bd):
 
 
 def test_mixed_without_refinement_is_plain_factor(bd):
-    Nc = np.array([40], np.int32)
+    """refine = 0: y = s Lt xi.  The product sums groups of four FP32
+    products (three roundings of at most u = 2^-24 of the group's absolute
+    sum) and adds the group sums exactly (two-sum), so every element is
+    within 4 u s sum_j |Lt_ij xi_j| of the FP64 product of the same Lt."""
+    Nc = np.array([40, 300], np.int32)
     r0 = inputs.random_walk(Nc, 33)
     ctx = bd.Context(Nc, precision=bd.MIXED_TF32, refine=0)
     ctx.set_state(cuda(r0))
     ctx.assemble()
     ctx.factor()
-    xi = inputs.gaussian_noise(1, 40, 34)[0]
-    y = ctx.brownian(cuda(xi)).cpu().numpy().ravel()
-    Lt = ctx.read_matrix(0, 1)
-    yref = np.sqrt(2e-4) * Lt @ xi.ravel()
-    assert np.abs(y - yref).max() / np.abs(yref).max() < 1e-9
+    xi = inputs.gaussian_noise(1, int(Nc.sum()), 34)[0]
+    y = ctx.brownian(cuda(xi)).cpu().numpy()
+    s = np.sqrt(2e-4)
+    off = np.concatenate([[0], np.cumsum(Nc)])
+    for c in range(len(Nc)):
+        sl = slice(off[c], off[c + 1])
+        Lt = ctx.read_matrix(c, 1)
+        x = xi[sl].ravel()
+        yref = s * Lt @ x
+        bound = 4 * 2.0 ** -24 * s * (np.abs(Lt) @ np.abs(x)) + 1e-300
+        assert (np.abs(y[sl].ravel() - yref) <= bound).all(), np.max(np.abs(y[sl].ravel() - yref) / bound)
     ctx.close()
 
 
