@@ -71,7 +71,8 @@ struct bd_ctx {
   cudaEvent_t gev[kMaxGroups + 1] = {};
   // concurrent branches of the step: the K chain, the refinement's solve
   cudaStream_t aux[2] = {};
-  cudaEvent_t aev[6] = {};  // [0,1] K-chain fork/join, [2,3] refinement fork/join, [4,5] caller-stream fence
+  cudaEvent_t aev[7] = {};  // [0,1] K-chain fork/join, [2,3] refinement fork/join, [4,5] caller-stream fence,
+                            // [6] mixed: rod directions and G formed
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // forward-mode tangent workspace (allocated by the first bd_adjoint call)
@@ -197,6 +198,7 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   if (c->mixed) {
     CK(launch_form_k_pos(c->r, (float*)c->K, c->G, c->d_cd, c->n_chains, c->max_m, c->uhat, c->ph.hstar,
                          c->ph.a, sk));
+    CK(cudaEventRecord(c->aev[6], sk));  // the predictor and the first product need only these
     CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64,
                        c->status, sk));
     CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
@@ -212,7 +214,8 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
   prof_mark(c, 2, s);
   if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
   prof_mark(c, 3, s);
-  CK(cudaStreamWaitEvent(s, c->aev[1], 0));
+  // mixed path: K's factor is awaited only before the first solve
+  CK(cudaStreamWaitEvent(s, c->aev[c->mixed ? 6 : 1], 0));
   CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
                       c->F, c->state, c->status, c->iters, c->mixed ? c->accurate : nullptr, s));
   prof_mark(c, 4, s);
@@ -223,13 +226,16 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
 // the residual from r(T) = r* + dt D F, the solve.  Mixed path: the rod-space
 // product w = G T (plain FP32 sums while a chain's residual is large,
 // compensated after, increments G dT once accurate), the residual from
-// Q(T) = Q* - dt w, the solve (which also records dT).
-int enqueue_newton_iter(bd_ctx* c, cudaStream_t s) {
+// Q(T) = Q* - dt w, the solve (which also records dT).  `first`: the step's
+// first iteration, whose solve waits for the end of the K chain (K's factor
+// and its super-block inverses) -- the product and residual run beside it.
+int enqueue_newton_iter(bd_ctx* c, cudaStream_t s, bool first = false) {
   if (c->mixed) {
     CK(launch_tension_products_g(c->G, c->d_cd, c->n_chains, c->max_mp, c->T, c->dT, c->u, c->state,
                                  c->accurate, s));
     CK(launch_newton_residual_g(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rhs, c->state, c->status,
                                 c->iters, c->accurate, s));
+    if (first) CK(cudaStreamWaitEvent(s, c->aev[1], 0));
     CK(launch_newton_solve_sb((const float*)c->K, c->Vsb, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs, c->T,
                               c->F, c->state, c->iters, c->dT, s));
     return BD_OK;
@@ -348,7 +354,9 @@ int build_step_graph(bd_ctx* c) {
   int rc = enqueue_pre_newton(c, s);
   // the first graph_unroll tension iterations are plain nodes (chains that
   // have converged skip them on the device); the WHILE node takes the rest
-  for (int i = 0; rc == BD_OK && i < c->graph_unroll; ++i) rc = enqueue_newton_iter(c, s);
+  for (int i = 0; rc == BD_OK && i < c->graph_unroll; ++i) rc = enqueue_newton_iter(c, s, i == 0);
+  if (rc == BD_OK && c->graph_unroll == 0 && c->mixed && cudaStreamWaitEvent(s, c->aev[1], 0) != cudaSuccess)
+    rc = BD_ERR_CUDA;
   c->while_cap = c->ph.max_newton + 3 - c->graph_unroll;
   if (c->while_cap < 1) c->while_cap = 1;
   cudaGraph_t g = nullptr;
@@ -415,7 +423,7 @@ int enqueue_step_direct(bd_ctx* c, cudaStream_t s) {
   prof_mark(c, 0, s);
   if ((rc = enqueue_pre_newton(c, s))) return rc;
   for (int it = 0; it < c->direct_iters; ++it)
-    if ((rc = enqueue_newton_iter(c, s))) return rc;
+    if ((rc = enqueue_newton_iter(c, s, it == 0))) return rc;
   prof_mark(c, 5, s);
   if ((rc = enqueue_finalize(c, s))) return rc;
   prof_mark(c, 6, s);
@@ -557,7 +565,7 @@ void bd_destroy(bd_ctx* c) {
     if (c->gev[g]) cudaEventDestroy(c->gev[g]);
   for (int g = 0; g < 2; ++g)
     if (c->aux[g]) cudaStreamDestroy(c->aux[g]);
-  for (int g = 0; g < 6; ++g)
+  for (int g = 0; g < 7; ++g)
     if (c->aev[g]) cudaEventDestroy(c->aev[g]);
   if (c->cs) cudaStreamDestroy(c->cs);
   if (c->cs2) cudaStreamDestroy(c->cs2);
@@ -716,7 +724,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
       cudaStreamCreateWithPriority(&c->aux[0], cudaStreamNonBlocking, pr_low) != cudaSuccess ||
       cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, pr_high) != cudaSuccess)
     return fail(BD_ERR_CUDA);
-  for (int g = 0; g < 6; ++g)
+  for (int g = 0; g < 7; ++g)
     if (cudaEventCreateWithFlags(&c->aev[g], cudaEventDisableTiming) != cudaSuccess)
       return fail(BD_ERR_CUDA);
   cudaStream_t s = c->cs;

@@ -11,6 +11,7 @@
 //   update64: A_ij -= L_ik L_jk^T for the trailing lower tiles.
 // The 64 x 64 diagonal-tile inverses are kept for the tension solve.
 #include "bd_internal.h"
+#include "pdl.h"
 #include "potrf_dev.h"
 
 namespace bd {
@@ -27,7 +28,9 @@ __global__ void __launch_bounds__(RegPotrf64::kThreads) k_potrf64(float* __restr
   if (k * K64 >= d.mp) return;
   float* base = K + d.koff + (long long)(k * K64) * d.mp + k * K64;
   float* wout = Kinv + (d.kwrow + (long long)k * K64) * K64;
+  grid_dep_wait();
   potrf_regs<K64>(base, d.mp, base, d.mp, wout, K64, sm);
+  grid_dep_launch();
   if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf64::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
 }
 
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, c
   const long long ldy = TRSM ? K64 : mp;
   float* out = base + (long long)(i * K64) * mp + (TRSM ? k : j) * K64;
   const int t = threadIdx.x;
+  grid_dep_wait();
 #pragma unroll
   for (int q = 0; q < K64 * K64 / 4 / kG64Threads; ++q) {
     const int e = t + kG64Threads * q;
@@ -121,6 +125,7 @@ __global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, c
         acc[a][b] = v;
       }
   }
+  grid_dep_launch();
   if (TRSM) __syncthreads();  // every read of Xs is done: it takes the result
   const bool diag = !TRSM && (i == j);
 #pragma unroll
@@ -155,16 +160,17 @@ bool is_k64_kernel(const void* f) {
 
 cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
                             int* status, cudaStream_t s) {
-  for (int k = 0; k < max_tiles; ++k) {
-    k_potrf64<<<n_chains, RegPotrf64::kThreads, 0, s>>>(K, Kinv, cd, k, status);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < max_tiles && e == cudaSuccess; ++k) {
+    e = launch_pdl(k_potrf64, dim3(n_chains), dim3(RegPotrf64::kThreads), 0, s, K, Kinv, cd, k, status);
     const int below = max_tiles - 1 - k;
-    if (below > 0) {
-      k_gemm64<true><<<dim3(below, n_chains), kG64Threads, g64_smem<true>(), s>>>(K, Kinv, cd, k);
-      k_gemm64<false><<<dim3(below * (below + 1) / 2, n_chains), kG64Threads, g64_smem<false>(), s>>>(K, Kinv,
-                                                                                                   cd, k);
-    }
+    if (below > 0 && e == cudaSuccess)
+      e = launch_pdl(k_gemm64<true>, dim3(below, n_chains), dim3(kG64Threads), g64_smem<true>(), s, K, Kinv, cd, k);
+    if (below > 0 && e == cudaSuccess)
+      e = launch_pdl(k_gemm64<false>, dim3(below * (below + 1) / 2, n_chains), dim3(kG64Threads), g64_smem<false>(),
+                     s, K, Kinv, cd, k);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace bd

@@ -21,12 +21,15 @@
 // tcgen05.ld, stage the tile in shared memory in the same swizzled layout, and
 // one TMA reduce-add (update) or store (panel solve) writes it to the matrix.
 // Operands are TF32 (10-bit mantissa), accumulation FP32.  No multicast.
+// All launches use programmatic dependent launch (pdl.h): a kernel's
+// prologue (barriers, TMEM allocation) overlaps the end of its predecessor.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
 #include <stdio.h>
 
 #include "bd_internal.h"
+#include "pdl.h"
 #include "potrf_dev.h"
 #include "tc_ptx.h"
 
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  grid_dep_wait();  // everything above overlaps the tail of the preceding kernel
 
   const CUtensorMap* am = maps + c;
   const CUtensorMap* bm = (MODE == TC_TRSM) ? wmap : maps + c;
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
     }
   }
   __syncwarp();
+  grid_dep_launch();  // the next kernel may start its prologue during this epilogue
 
   // ---- epilogue (all four warps; warp w owns TMEM lanes / tile rows 32w..)
   const bool got = mbar_wait(done, 0);
@@ -264,7 +269,9 @@ __global__ void __launch_bounds__(RegPotrf128::kThreads) k_potrf128(float* __res
   if (k * NB >= d.np) return;
   float* base = M + d.moff + (long long)(k * NB) * d.np + k * NB;
   float* wout = Winv + ((long long)d.wrow + (long long)k * NB) * NB;
+  grid_dep_wait();
   potrf_regs<NB>(base, d.np, base, d.np, wout, NB, sm);
+  grid_dep_launch();
   if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf128::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_NOT_PD);
 }
 
@@ -329,22 +336,25 @@ cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const
                            cudaStream_t s) {
   const int T = max_tiles;
   if (panel < 1) panel = 1;
-  for (int K0 = 0; K0 < T; K0 += panel) {
+  cudaError_t e = cudaSuccess;
+  for (int K0 = 0; K0 < T && e == cudaSuccess; K0 += panel) {
     const int K1 = K0 + panel < T ? K0 + panel : T;
-    for (int k = K0; k < K1; ++k) {
+    for (int k = K0; k < K1 && e == cudaSuccess; ++k) {
       if (k > K0)
-        k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, k, k + 1), n_chains), 128, kTcSmem, s>>>(
-            maps, nullptr, cd, K0, k, k, k + 1, status);
-      k_potrf128<<<n_chains, RegPotrf128::kThreads, 0, s>>>(M, Winv, cd, k, status);
+        e = launch_pdl(k_tc_gemm<TC_UPDATE>, dim3(update_tiles(T, k, k + 1), n_chains), dim3(128), kTcSmem, s,
+                       maps, (const CUtensorMap*)nullptr, cd, K0, k, k, k + 1, status);
+      if (e == cudaSuccess)
+        e = launch_pdl(k_potrf128, dim3(n_chains), dim3(RegPotrf128::kThreads), 0, s, M, Winv, cd, k, status);
       const int below = T - 1 - k;
-      if (below > 0)
-        k_tc_gemm<TC_TRSM><<<dim3(below, n_chains), 128, kTcSmem, s>>>(maps, wmap, cd, k, k + 1, 0, 0,
-                                                                       status);
+      if (below > 0 && e == cudaSuccess)
+        e = launch_pdl(k_tc_gemm<TC_TRSM>, dim3(below, n_chains), dim3(128), kTcSmem, s, maps, wmap, cd, k,
+                       k + 1, 0, 0, status);
     }
-    if (K1 < T)
-      k_tc_gemm<TC_UPDATE><<<dim3(update_tiles(T, K1, T), n_chains), 128, kTcSmem, s>>>(
-          maps, nullptr, cd, K0, K1, K1, T, status);
+    if (K1 < T && e == cudaSuccess)
+      e = launch_pdl(k_tc_gemm<TC_UPDATE>, dim3(update_tiles(T, K1, T), n_chains), dim3(128), kTcSmem, s, maps,
+                     (const CUtensorMap*)nullptr, cd, K0, K1, K1, T, status);
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

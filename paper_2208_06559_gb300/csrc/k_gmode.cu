@@ -19,6 +19,7 @@
 //   k_finalize_g     : positions of converged chains from the rods.
 #include "bd_internal.h"
 #include "block_dev.h"
+#include "pdl.h"
 
 namespace bd {
 
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__
                                                        const int* __restrict__ mode) {
   extern __shared__ __align__(16) float4 tsm[];  // [mp / 4] hi words, then [mp / 4] lo words
   const int c = blockIdx.y;
+  grid_dep_wait();
   if (state[c] >= NS_DONE) return;
   const ChainDesc d = cd[c];
   const int mp = d.mp, m = d.m, mp4 = mp >> 2;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(kGvThreads) k_gemv_g(const float* __restrict__
         *wp = v;
     }
   }
+  grid_dep_launch();
 }
 
 // One CTA per chain: Q_k = Q*_k - dt w_k, g_k = |Q_k|^2 - 1, max |g|, and the
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(256) k_newton_residual_g(const double* __restr
                                                            int* __restrict__ mode) {
   __shared__ double red[32];
   const int c = blockIdx.x;
+  grid_dep_wait();
   const int st = state[c];
   if (st >= NS_DONE) return;
   if (status[c] != BD_OK) {
@@ -280,16 +284,15 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __r
 cudaError_t launch_tension_products_g(const float* G, const ChainDesc* cd, int n_chains, int max_mp,
                                       const double* T, const double* dT, double* w, const int* state,
                                       const int* mode, cudaStream_t s) {
-  k_gemv_g<<<dim3(ceil_div(3 * max_mp, kGvRows), n_chains), kGvThreads, (size_t)max_mp * 2 * sizeof(float),
-             s>>>(G, cd, T, dT, w, state, mode);
-  return cudaGetLastError();
+  return launch_pdl(k_gemv_g, dim3(ceil_div(3 * max_mp, kGvRows), n_chains), dim3(kGvThreads),
+                    (size_t)max_mp * 2 * sizeof(float), s, G, cd, T, dT, w, state, mode);
 }
 
 cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const ChainDesc* cd,
                                      int n_chains, Phys ph, double* rhs, int* state, int* status,
                                      const int* iters, int* mode, cudaStream_t s) {
-  k_newton_residual_g<<<n_chains, 256, 0, s>>>(rstar, w, cd, ph, rhs, state, status, iters, mode);
-  return cudaGetLastError();
+  return launch_pdl(k_newton_residual_g, dim3(n_chains), dim3(256), 0, s, rstar, w, cd, ph, rhs, state, status,
+                    iters, mode);
 }
 
 cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const float* M, const double* rstar,

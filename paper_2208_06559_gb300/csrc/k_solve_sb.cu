@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include "bd_internal.h"
+#include "pdl.h"
 
 namespace bd {
 
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __res
   float* Vs = V + (d.kwrow + (long long)kSB * S) * kSB;  // V_S row r at r * kSB
   const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
   const int J0 = kSBBlocks * S;
+  grid_dep_wait();
   auto store_block = [&](int i) {  // X[i] -> V_S rows 64 i.., columns 64 j..
     for (int e = t; e < 64 * 64; e += kSbInvThreads) {
       const int r = e >> 6, cc = e & 63;
@@ -152,6 +154,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
   __shared__ __align__(16) float xb[2][kSB];  // exchanged partial results, by exchange parity
   __shared__ __align__(16) float sv[kSB];
   const int c = blockIdx.x >> 1;
+  grid_dep_wait();
   const int st = state[c];
   if (st != NS_ACTIVE && st != NS_EXTRA) return;  // the same for both CTAs of the cluster
   const ChainDesc d = cd[c];
@@ -300,6 +303,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
     __syncthreads();
   }
   cl.sync();  // no CTA leaves while its partner may still read its shared memory
+  grid_dep_launch();
   if (rank != 0) return;
   for (int k = t; k < m; k += kSbThreads) {
     Tn[d.roff + k] += (double)zs[k];
@@ -321,16 +325,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
 cudaError_t launch_sb_inverse(const float* K, const float* Kinv, float* V, const ChainDesc* cd, int n_chains,
                               int max_mp, cudaStream_t s) {
   const int nsb = ceil_div(max_mp, kSB);
-  k_sb_inverse<<<dim3(nsb * kSBBlocks, n_chains), kSbInvThreads, kSbInvSmem, s>>>(K, Kinv, V, cd);
-  return cudaGetLastError();
+  return launch_pdl(k_sb_inverse, dim3(nsb * kSBBlocks, n_chains), dim3(kSbInvThreads), kSbInvSmem, s, K, Kinv, V,
+                    cd);
 }
 
 cudaError_t launch_newton_solve_sb(const float* K, const float* V, const ChainDesc* cd, int n_chains, Phys ph,
                                    const double* uhat, const double* rhs, double* Tn, double* F, int* state,
                                    int* iters, double* dT, cudaStream_t s) {
-  k_newton_solve_sb<<<2 * n_chains, kSbThreads, 2 * kSbMaxM * sizeof(float), s>>>(K, V, cd, ph, uhat, rhs, Tn,
-                                                                                  F, state, iters, dT);
-  return cudaGetLastError();
+  return launch_pdl(k_newton_solve_sb, dim3(2 * n_chains), dim3(kSbThreads), 2 * kSbMaxM * sizeof(float), s, K, V,
+                    cd, ph, uhat, rhs, Tn, F, state, iters, dT);
 }
 
 bool is_sb_inverse_kernel(const void* f) { return f == (const void*)k_sb_inverse; }
