@@ -34,9 +34,10 @@ __global__ void __launch_bounds__(RegPotrf64::kThreads) k_potrf64(float* __restr
   if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf64::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_CONSTRAINT);
 }
 
-// 64 x 64 output tile, 64 threads, 8 x 8 outputs each.  The operands (and,
-// for the update, the output tile itself) are copied row-major into shared
-// memory with cp.async, all copies in flight at once.  Thread (i, j) =
+// 64 x 64 output tile, 64 threads, 8 x 8 outputs each.  The operands are
+// copied row-major into shared memory with cp.async, all copies in flight at
+// once; the update's output tile is copied into the first operand's buffer
+// once the products are done (two tiles of shared memory: six CTAs per SM).  Thread (i, j) =
 // (t % 8, t / 8) owns rows i + 8a and columns j + 8b (a, b < 8): per four k
 // it reads eight 16-byte row slices of each operand (rows 4 banks apart
 // across a warp: no bank conflicts) for 256 FMAs.  The result is written back
@@ -49,7 +50,7 @@ constexpr int kG64Tile = K64 * kG64P;
 
 template <bool TRSM>
 constexpr int g64_smem() {
-  return (TRSM ? 2 : 3) * kG64Tile * (int)sizeof(float);
+  return 2 * kG64Tile * (int)sizeof(float);
 }
 
 __device__ __forceinline__ void g64_cp16(float* smem, const float* gmem) {
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, c
   extern __shared__ __align__(16) float g64s[];
   float (*Xs)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s);
   float (*Ys)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s + kG64Tile);
-  float (*Cs)[kG64P] = reinterpret_cast<float (*)[kG64P]>(g64s + (TRSM ? 0 : 2 * kG64Tile));
+  float (*Cs)[kG64P] = Xs;  // the output tile, after the products
   const ChainDesc d = cd[blockIdx.y];
   const int T = d.mp / K64;
   int i, j;
@@ -96,7 +97,6 @@ __global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, c
     const int r = e >> 4, c4 = (e & 15) * 4;
     g64_cp16(&Xs[r][c4], xs + r * mp + c4);
     g64_cp16(&Ys[r][c4], ys + r * ldy + c4);
-    if (!TRSM) g64_cp16(&Cs[r][c4], out + r * mp + c4);
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   __syncthreads();
@@ -126,7 +126,17 @@ __global__ void __launch_bounds__(kG64Threads) k_gemm64(float* __restrict__ K, c
       }
   }
   grid_dep_launch();
-  if (TRSM) __syncthreads();  // every read of Xs is done: it takes the result
+  __syncthreads();  // every read of Xs is done: it takes the output tile
+  if (!TRSM) {
+#pragma unroll
+    for (int q = 0; q < K64 * K64 / 4 / kG64Threads; ++q) {
+      const int e = t + kG64Threads * q;
+      const int r = e >> 4, c4 = (e & 15) * 4;
+      g64_cp16(&Cs[r][c4], out + r * mp + c4);
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  }
   const bool diag = !TRSM && (i == j);
 #pragma unroll
   for (int a = 0; a < 8; ++a)
