@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
     }
   }
   __syncthreads();
+  const float inv_a = 1.0f / arad;
   for (int e = t; e < KB * KB; e += blockDim.x) {
     const int x = e / KB, y = e % KB;
     const int a = KR * kt + x, b = KR * lt + y;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
 #pragma unroll
         for (int q = 0; q < 3; ++q) R[q] = (ph[0][x][q] - ph[1][y][q]) + (pl[0][x][q] - pl[1][y][q]);
         float ci, cr;
-        rpy_coeffs<float>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, arad, ci, cr);
+        rpy_coeffs_rsqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, arad, inv_a, ci, cr);
         const float c0 = cr * R[0], c1 = cr * R[1];
         dv[0] = fmaf(c0, R[0], ci);
         dv[1] = c0 * R[1];

@@ -1,5 +1,5 @@
-// rpy_dev.h -- RPY pair coefficients (Sec. 3 Eqs. (8)-(9)), shared by the
-// assembly of D and the formation of the rod-coupling matrix from positions.
+// rpy_dev.h -- RPY pair coefficients (Sec. 3 Eqs. (8)-(9)), for the assembly
+// of D and the formation of the rod-coupling matrices from positions.
 #pragma once
 
 namespace bd {
@@ -21,6 +21,37 @@ __device__ __forceinline__ void rpy_coeffs(C R2, C hstar, C a, C& cI, C& cRR) {
     const C pref = C(0.375) * hstar / a;
     cI = pref * (C(8) / C(3) - C(0.75) * Rn / a);
     cRR = (Rn > C(0)) ? pref * (C(0.25) / a) / Rn : C(0);
+  }
+}
+
+// The same coefficients in FP32 from one reciprocal square root (rsqrtf, a
+// few ulp) and a precomputed 1 / a instead of a square root and three
+// divisions: a relative change of order 1e-7, the size of the FP32 rounding
+// itself.  For the formation of K and G from the positions, which evaluates
+// one pair per output element and is instruction-bound.
+__device__ __forceinline__ void rpy_coeffs_rsqrt(float R2, float hstar, float a, float inv_a, float& cI,
+                                                 float& cRR) {
+  if (hstar == 0.0f) {
+    cI = 0.0f;
+    cRR = 0.0f;
+    return;
+  }
+  if (R2 >= 4.0f * a * a) {  // R >= 2a
+    const float iR = rsqrtf(R2);
+    const float pref = 0.75f * hstar * iR;
+    const float a2R2 = a * a * iR * iR;
+    cI = pref * (1.0f + (2.0f / 3.0f) * a2R2);
+    cRR = pref * (1.0f - 2.0f * a2R2) * iR * iR;
+  } else {
+    const float pref = 0.375f * hstar * inv_a;
+    if (R2 > 0.0f) {
+      const float iR = rsqrtf(R2);
+      cI = pref * (8.0f / 3.0f - 0.75f * (R2 * iR) * inv_a);
+      cRR = pref * (0.25f * inv_a) * iR;
+    } else {
+      cI = pref * (8.0f / 3.0f);
+      cRR = 0.0f;
+    }
   }
 }
 
