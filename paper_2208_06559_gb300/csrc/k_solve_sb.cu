@@ -28,21 +28,22 @@ constexpr int kSB = 256;             // super-block order
 constexpr int kSBBlocks = kSB / 64;  // 64-wide blocks per super-block
 constexpr int kTP = 65;              // shared-memory pitch of a 64 x 64 tile
 constexpr int kSbInvThreads = 256;
-constexpr int kSbInvSmem = (kSBBlocks + 2) * 64 * kTP * (int)sizeof(float);
+constexpr int kSbInvSmem = 3 * 64 * kTP * (int)sizeof(float);
 constexpr int kSbThreads = 1024;
 constexpr int kSbMaxM = 4096;        // rods per chain (N <= 4096 beads)
 
 // One CTA per (chain, super-block S, column block j): V_S's column block j,
-// rows j .. end of the super-block.  The column is built top-down in shared
-// memory (X[i] = V_ij) and each finished block is stored to V.
+// rows j .. end of the super-block, top-down.  Each finished block V_ij goes
+// straight to V and is read back (from L2) as an operand of the blocks below
+// it, so only three 64 x 64 tiles live in shared memory (four CTAs per SM).
 __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __restrict__ K,
                                                               const float* __restrict__ Kinv,
                                                               float* __restrict__ V,
                                                               const ChainDesc* __restrict__ cd) {
   extern __shared__ float sbi_smem[];
-  float (*X)[64][kTP] = reinterpret_cast<float (*)[64][kTP]>(sbi_smem);  // [kSBBlocks]
-  float (*At)[kTP] = reinterpret_cast<float (*)[kTP]>(sbi_smem + kSBBlocks * 64 * kTP);
-  float (*Wt)[kTP] = reinterpret_cast<float (*)[kTP]>(sbi_smem + (kSBBlocks + 1) * 64 * kTP);
+  float (*At)[kTP] = reinterpret_cast<float (*)[kTP]>(sbi_smem);
+  float (*Bt)[kTP] = reinterpret_cast<float (*)[kTP]>(sbi_smem + 64 * kTP);
+  float (*Wt)[kTP] = reinterpret_cast<float (*)[kTP]>(sbi_smem + 2 * 64 * kTP);
   const ChainDesc d = cd[blockIdx.y];
   const int S = blockIdx.x / kSBBlocks, j = blockIdx.x % kSBBlocks;
   const int nb = d.mp / 64;
@@ -55,29 +56,27 @@ __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __res
   const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
   const int J0 = kSBBlocks * S;
   grid_dep_wait();
-  auto store_block = [&](int i) {  // X[i] -> V_S rows 64 i.., columns 64 j..
-    for (int e = t; e < 64 * 64; e += kSbInvThreads) {
-      const int r = e >> 6, cc = e & 63;
-      Vs[(long long)(64 * i + r) * kSB + 64 * j + cc] = X[i][r][cc];
-    }
-  };
-  for (int e = t; e < 64 * 64; e += kSbInvThreads) {
-    const int r = e >> 6, cc = e & 63;
-    X[j][r][cc] = W[(long long)(64 * (J0 + j) + r) * 64 + cc];  // zero above the diagonal
+  auto vblk = [&](int i) { return Vs + (long long)(64 * i) * kSB + 64 * j; };  // V_ij, row pitch kSB
+  // V_jj = W_j (zero above the diagonal)
+  for (int e = t; e < 64 * 16; e += kSbInvThreads) {
+    const int r = e >> 4, c4 = (e & 15) * 4;
+    *reinterpret_cast<float4*>(vblk(j) + (long long)r * kSB + c4) =
+        *reinterpret_cast<const float4*>(W + (long long)(64 * (J0 + j) + r) * 64 + c4);
   }
-  __syncthreads();
-  store_block(j);
+  __syncthreads();  // V_jj is visible to the whole CTA before it is read back
   for (int i = j + 1; i < nbS; ++i) {
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-    for (int k = j; k < i; ++k) {  // acc += L_ik X_k
+    for (int k = j; k < i; ++k) {  // acc += L_ik V_kj
       const float* Lik = L + (long long)(64 * (J0 + i)) * mp + 64 * (J0 + k);
+      const float* Vk = vblk(k);
       for (int e = t; e < 64 * 64; e += kSbInvThreads) {
         const int r = e >> 6, cc = e & 63;
         At[r][cc] = Lik[(long long)r * mp + cc];
+        Bt[r][cc] = __ldcg(Vk + (long long)r * kSB + cc);
       }
       __syncthreads();
 #pragma unroll 4
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __res
 #pragma unroll
         for (int a = 0; a < 4; ++a) av[a] = At[4 * tr + a][q];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = X[k][q][4 * tc + b];
+        for (int b = 0; b < 4; ++b) bv[b] = Bt[q][4 * tc + b];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -94,7 +93,7 @@ __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __res
       }
       __syncthreads();
     }
-    // X_i = -W_i acc
+    // V_ij = -W_i acc
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -120,12 +119,12 @@ __global__ void __launch_bounds__(kSbInvThreads) k_sb_inverse(const float* __res
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
     }
+    float* Vi = vblk(i);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) X[i][4 * tr + a][4 * tc + b] = -acc[a][b];
-    __syncthreads();  // X[i] complete; At and Wt free for the next row block
-    store_block(i);
+      *reinterpret_cast<float4*>(Vi + (long long)(4 * tr + a) * kSB + 4 * tc) =
+          make_float4(-acc[a][0], -acc[a][1], -acc[a][2], -acc[a][3]);
+    __syncthreads();  // V_ij visible; At and Wt free for the next row block
   }
 }
 
