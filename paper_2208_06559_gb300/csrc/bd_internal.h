@@ -13,6 +13,7 @@
 //   * FP64 (BD_FP64) or FP32 (mixed) element type for both matrices.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,13 +189,16 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
                                 cudaEvent_t* ev);
 
 // Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
-bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains);
+bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, const ChainDesc* h_cd,
+                  int n_chains);
 cudaError_t tc_configure();
 // Factor chains [0, n_chains) of the given arrays (pointers may be offset to
-// a chain subrange); wmap is the TMA map of Winv.
+// a chain subrange); wmap is the TMA map of Winv; maps16 map the FP16 copies
+// of the off-diagonal L tiles (same layout as M), written by the panel
+// solves and read by the trailing updates.
 cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
-                           const ChainDesc* cd, int n_chains, int max_tiles, int panel, int* status,
-                           cudaStream_t s);
+                           const CUtensorMap* maps16, const ChainDesc* cd, int n_chains, int max_tiles,
+                           int panel, int* status, cudaStream_t s);
 
 // Forward-mode tangents of the FP64 step (k_tangent.cu).
 cudaError_t launch_assemble_dot(const double* r, const double* rdot, const ChainDesc* cd, int n_chains,

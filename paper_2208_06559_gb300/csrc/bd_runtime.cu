@@ -49,7 +49,8 @@ struct bd_ctx {
   float* Vsb = nullptr;            // mixed: inverses of the 256-wide diagonal super-blocks of K's factor
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
-  CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, then Winv)
+  CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, Winv, one per chain FP16 copy)
+  __half* M16 = nullptr;           // mixed: FP16 copies of the off-diagonal L tiles, layout of M
   double* stage = nullptr;  // staging for host-memory noise / observables
   size_t stage_elems = 0;
   int *status = nullptr, *state = nullptr, *iters = nullptr;
@@ -114,8 +115,9 @@ struct DeviceGuard {
 int enqueue_factor(bd_ctx* c, cudaStream_t s) {
   if (c->mixed) {
     const CUtensorMap* wmap = c->tmaps + c->n_chains;
+    const CUtensorMap* maps16 = c->tmaps + c->n_chains + 1;
     if (c->n_groups <= 1) {
-      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps, wmap, c->d_cd, c->n_chains,
+      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps, wmap, maps16, c->d_cd, c->n_chains,
                         c->max_np / kMixedTile, c->panel, c->status, s));
       return BD_OK;
     }
@@ -124,7 +126,7 @@ int enqueue_factor(bd_ctx* c, cudaStream_t s) {
     for (int g = 0; g < c->n_groups; ++g) {
       CK(cudaStreamWaitEvent(c->gs[g], c->gev[c->kMaxGroups], 0));
       const int c0 = c->group_start[g], c1 = c->group_start[g + 1];
-      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps + c0, wmap, c->d_cd + c0, c1 - c0,
+      CK(launch_chol_tc((float*)c->M, c->Winv, c->tmaps + c0, wmap, maps16 + c0, c->d_cd + c0, c1 - c0,
                         c->group_tiles[g], c->panel, c->status + c0, c->gs[g]));
       CK(cudaEventRecord(c->gev[g], c->gs[g]));
     }
@@ -554,7 +556,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
   for (void* b : bufs)
@@ -701,7 +703,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
          alloc((void**)&c->fsplit, (size_t)swrow * sizeof(float2)) &&
          alloc((void**)&c->dT, rr) && alloc((void**)&c->G, 3 * c->K_elems * sizeof(float)) &&
          alloc((void**)&c->Vsb, (size_t)kwrow * 256 * sizeof(float)) &&
-         alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (c->n_chains + 1));
+         alloc((void**)&c->M16, c->M_elems * sizeof(__half)) &&
+         alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (2 * c->n_chains + 1));
   if (!ok) {
     bd_destroy(c);
     return BD_ERR_OOM;
@@ -736,8 +739,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
       if (cudaEventCreateWithFlags(&c->gev[g], cudaEventDisableTiming) != cudaSuccess)
         return fail(BD_ERR_CUDA);
-    std::vector<CUtensorMap> hm(c->n_chains + 1);
-    if (!make_tc_maps(hm.data(), (float*)c->M, c->Winv, c->h_cd.data(), c->n_chains))
+    std::vector<CUtensorMap> hm(2 * c->n_chains + 1);
+    if (!make_tc_maps(hm.data(), (float*)c->M, c->Winv, c->M16, c->h_cd.data(), c->n_chains))
       return fail(BD_ERR_CUDA);
     if (cudaMemcpy(c->tmaps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||

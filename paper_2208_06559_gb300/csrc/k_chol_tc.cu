@@ -73,6 +73,7 @@ __device__ __forceinline__ bool tile_of(int mode, int p, int T, int k0, int j0, 
 template <int MODE>
 __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restrict__ maps,
                                                     const CUtensorMap* __restrict__ wmap,
+                                                    const CUtensorMap* __restrict__ maps16,
                                                     const ChainDesc* __restrict__ cd, int k0, int k1,
                                                     int j0, int j1, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
@@ -109,14 +110,19 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
   const uint32_t tmem = *tmem_slot;
   grid_dep_wait();  // everything above overlaps the tail of the preceding kernel
 
-  const CUtensorMap* am = maps + c;
-  const CUtensorMap* bm = (MODE == TC_TRSM) ? wmap : maps + c;
-  const int nchunks = (MODE == TC_TRSM) ? 4 : 4 * (k1 - k0);
+  // TRSM: FP32 operands (32-column slices), rounded to TF32 in shared memory.
+  // UPDATE: the FP16 copies of the L tiles (64-column slices, the same
+  // 32 KB per stage, twice the depth); the result goes to the FP32 matrix.
+  const CUtensorMap* om = maps + c;  // FP32 matrix: the output
+  const CUtensorMap* am = (MODE == TC_TRSM) ? maps + c : maps16 + c;
+  const CUtensorMap* bm = (MODE == TC_TRSM) ? wmap : maps16 + c;
+  const int nchunks = (MODE == TC_TRSM) ? 4 : 2 * (k1 - k0);
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
     prefetch_tmap(am);
     if (MODE == TC_TRSM) prefetch_tmap(bm);
+    else prefetch_tmap(om);
     for (int q = 0; q < nchunks; ++q) {
       const int s = q % kStages, round = q / kStages;
       if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
       uint8_t* sa = smem + s * kStageBytes;
       uint8_t* sb = sa + kChunkBytes;
       mbar_arrive_expect_tx(&full[s], kStageBytes);
-      const int kx = k0 * NB + 32 * q;  // column of the K slice in the matrix
+      const int kx = k0 * NB + (MODE == TC_TRSM ? 32 : 64) * q;  // column of the K slice in the matrix
       tma_load_2d(sa, am, &full[s], kx, ti * NB);
       if (MODE == TC_TRSM)
         tma_load_2d(sb, bm, &full[s], 32 * q, d.wrow + k0 * NB);
@@ -136,7 +142,7 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
   } else if (warp == 1) {
     // ---- MMA issuer (lane 0).  TRSM: the whole warp first meets the two
     // rounding warps on the stage's named barrier.
-    constexpr uint32_t idesc = idesc_mma(2u /*tf32*/, 128u, 128u);
+    constexpr uint32_t idesc = idesc_mma(MODE == TC_TRSM ? 2u /*tf32*/ : 0u /*f16*/, 128u, 128u);
     bool ok = true;
     for (int q = 0; q < nchunks; ++q) {
       const int s = q % kStages, round = q / kStages;
@@ -154,8 +160,12 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
         const uint32_t sa = smem_u32(smem + s * kStageBytes);
         const uint64_t ad = desc_sw128(sa), bdsc = desc_sw128(sa + kChunkBytes);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)  // K = 8 tf32 per MMA = 32 bytes of the 128-byte row
-          mma_tf32(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {  // K = 8 tf32 / 16 f16 per MMA = 32 bytes of the 128-byte row
+          if (MODE == TC_TRSM)
+            mma_tf32(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+          else
+            mma_f16(tmem, ad + 2 * kk, bdsc + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+        }
         mma_commit(&empty[s]);
       }
       __syncwarp();
@@ -231,9 +241,9 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
       for (int q = 0; q < 4; ++q) {
         const float* src = stage_out + q * (kChunkBytes / 4);
         if (MODE == TC_UPDATE)
-          tma_reduce_add_2d(am, src, tj * NB + 32 * q, ti * NB);
+          tma_reduce_add_2d(om, src, tj * NB + 32 * q, ti * NB);
         else
-          tma_store_2d(am, src, k0 * NB + 32 * q, ti * NB);
+          tma_store_2d(om, src, k0 * NB + 32 * q, ti * NB);
       }
       bulk_commit();
       bulk_wait_all();
@@ -242,6 +252,48 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
     }
   }
   __syncthreads();
+  if (MODE == TC_TRSM && *(volatile int*)fail == 0) {
+    // The FP16 copy of the L tile for the trailing updates, through the same
+    // shared memory (the FP32 tile's store has completed): each thread
+    // converts its own row, 128-byte rows of 64 halves swizzled like the
+    // FP32 chunks, FP16 chunk h (columns 64 h ..) over FP32 chunk 2 + h --
+    // chunks 2 and 3 are read before either is overwritten.
+    uint32_t hi_half[32];
+    const float* rowf = stage_out + row * 32;
+    auto granule = [&](int g, uint32_t* out4) {  // columns 8 g .. 8 g + 7 -> 4 half2 words
+      const int q = g >> 2, j4 = (2 * g) & 7;    // FP32 chunk, first float4 within it
+      const float4 a = *reinterpret_cast<const float4*>(rowf + q * (kChunkBytes / 4) + 4 * (j4 ^ (row & 7)));
+      const float4 b = *reinterpret_cast<const float4*>(rowf + q * (kChunkBytes / 4) + 4 * ((j4 + 1) ^ (row & 7)));
+      const half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+      const half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+      out4[0] = *reinterpret_cast<const uint32_t*>(&h0);
+      out4[1] = *reinterpret_cast<const uint32_t*>(&h1);
+      out4[2] = *reinterpret_cast<const uint32_t*>(&h2);
+      out4[3] = *reinterpret_cast<const uint32_t*>(&h3);
+    };
+#pragma unroll
+    for (int g = 0; g < 8; ++g) granule(8 + g, hi_half + 4 * g);  // columns 64 .. 127
+    uint8_t* h16 = smem + 2 * kChunkBytes + row * 128;            // FP16 chunk 0 (over FP32 chunk 2)
+    uint32_t lo_half[4];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      granule(g, lo_half);
+      *reinterpret_cast<uint4*>(h16 + 16 * (g ^ (row & 7))) = make_uint4(lo_half[0], lo_half[1], lo_half[2], lo_half[3]);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      *reinterpret_cast<uint4*>(h16 + kChunkBytes + 16 * (g ^ (row & 7))) =
+          make_uint4(hi_half[4 * g], hi_half[4 * g + 1], hi_half[4 * g + 2], hi_half[4 * g + 3]);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int h = 0; h < 2; ++h)
+        tma_store_2d(maps16 + c, smem + (2 + h) * kChunkBytes, k0 * NB + 64 * h, ti * NB);
+      bulk_commit();
+      bulk_wait_all();
+    }
+    __syncthreads();
+  }
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tmem, 128);
@@ -302,12 +354,28 @@ static bool encode_f32(CUtensorMap* out, void* base, uint64_t cols, uint64_t row
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Fills maps[0..n_chains) (one per chain's matrix) and maps[n_chains] (Winv,
-// [sum_c np_c][128]).
-bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, const ChainDesc* h_cd, int n_chains) {
+static bool encode_f16(CUtensorMap* out, void* base, uint64_t cols, uint64_t rows, uint64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)NB};  // 128-byte rows
+  cuuint32_t es[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Fills maps[0..n_chains) (one per chain's matrix), maps[n_chains] (Winv,
+// [sum_c np_c][128]) and maps[n_chains + 1 + c] (chain c's FP16 copy of the
+// L tiles, same layout as its matrix).
+bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, const ChainDesc* h_cd,
+                  int n_chains) {
   uint64_t wrows = 0;
   for (int c = 0; c < n_chains; ++c) {
     if (!encode_f32(&host_maps[c], M + h_cd[c].moff, h_cd[c].np, h_cd[c].np, h_cd[c].np)) return false;
+    if (!encode_f16(&host_maps[n_chains + 1 + c], M16 + h_cd[c].moff, h_cd[c].np, h_cd[c].np, h_cd[c].np))
+      return false;
     wrows += h_cd[c].np;
   }
   return encode_f32(&host_maps[n_chains], Winv, NB, wrows, NB);
@@ -332,8 +400,8 @@ static int update_tiles(int T, int j0, int j1) {
 }
 
 cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const CUtensorMap* wmap,
-                           const ChainDesc* cd, int n_chains, int max_tiles, int panel, int* status,
-                           cudaStream_t s) {
+                           const CUtensorMap* maps16, const ChainDesc* cd, int n_chains, int max_tiles,
+                           int panel, int* status, cudaStream_t s) {
   const int T = max_tiles;
   if (panel < 1) panel = 1;
   cudaError_t e = cudaSuccess;
@@ -342,17 +410,17 @@ cudaError_t launch_chol_tc(float* M, float* Winv, const CUtensorMap* maps, const
     for (int k = K0; k < K1 && e == cudaSuccess; ++k) {
       if (k > K0)
         e = launch_pdl(k_tc_gemm<TC_UPDATE>, dim3(update_tiles(T, k, k + 1), n_chains), dim3(128), kTcSmem, s,
-                       maps, (const CUtensorMap*)nullptr, cd, K0, k, k, k + 1, status);
+                       maps, (const CUtensorMap*)nullptr, maps16, cd, K0, k, k, k + 1, status);
       if (e == cudaSuccess)
         e = launch_pdl(k_potrf128, dim3(n_chains), dim3(RegPotrf128::kThreads), 0, s, M, Winv, cd, k, status);
       const int below = T - 1 - k;
       if (below > 0 && e == cudaSuccess)
-        e = launch_pdl(k_tc_gemm<TC_TRSM>, dim3(below, n_chains), dim3(128), kTcSmem, s, maps, wmap, cd, k,
+        e = launch_pdl(k_tc_gemm<TC_TRSM>, dim3(below, n_chains), dim3(128), kTcSmem, s, maps, wmap, maps16, cd, k,
                        k + 1, 0, 0, status);
     }
     if (K1 < T && e == cudaSuccess)
       e = launch_pdl(k_tc_gemm<TC_UPDATE>, dim3(update_tiles(T, K1, T), n_chains), dim3(128), kTcSmem, s, maps,
-                     (const CUtensorMap*)nullptr, cd, K0, K1, K1, T, status);
+                     (const CUtensorMap*)nullptr, maps16, cd, K0, K1, K1, T, status);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
