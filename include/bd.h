@@ -61,10 +61,16 @@ extern "C" {
 typedef struct bd_ctx bd_ctx; /* opaque, library-owned */
 
 typedef enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2 } bd_flow;
-/* BD_FP64: every stage in FP64.  BD_MIXED_TF32 / BD_MIXED_BF16: D and B stored
- * in FP32, Cholesky trailing updates on the tensor cores (TF32 or BF16
- * operands, FP32 accumulation), FP64 diagonal-block factorisation, one
- * refinement step on the Brownian displacement, FP64 tension solve. */
+/* BD_FP64: every stage in FP64.
+ * BD_MIXED_TF32: D and its factor stored in FP32; FP32 diagonal tiles of the
+ * factor; panel solves on the tensor cores with operands rounded to TF32
+ * (round to nearest), the factor's tiles stored so rounded; trailing updates
+ * on the tensor cores from FP16 copies of those tiles (the same 10-bit
+ * mantissa; |L_ij| <= 1 since D has a unit diagonal), FP32 accumulation;
+ * one refinement step on the Brownian displacement; the tension iteration
+ * with FP64-level (double-float) products, so rods hold to the tolerance.
+ * BD_MIXED_BF16: accepted and run exactly as BD_MIXED_TF32 -- BF16 operands
+ * (8-bit mantissa) would leave the refined factor's error above 1e-6. */
 typedef enum { BD_FP64 = 0, BD_MIXED_TF32 = 1, BD_MIXED_BF16 = 2 } bd_precision;
 typedef enum { BD_RIGID = 0, BD_FRAENKEL = 1 } bd_constraint;
 
