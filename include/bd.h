@@ -206,16 +206,18 @@ int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noi
  * The tensor-core factorisation has two shape parameters: the super-panel
  * width (tile columns whose trailing update is applied together, K = 128 x
  * panel) and the number of chain groups factored concurrently on separate
- * streams.  bd_tune_factor times every combination of panel {2, 4, 6, 8, 12}
- * and groups {1, 2, 4, 8, 12, 16} (groups <= chains) on the context's current
- * positions,
+ * streams.  A panel at least as wide as a chain's tile count makes the
+ * factorisation left-looking (every column receives all earlier columns'
+ * updates at once, no trailing update).  bd_tune_factor times every
+ * combination of panel {2, 4, 6, 8, 12, 16, 24} and groups {1, 2, 4, 8, 12,
+ * 16} (groups <= chains) on the context's current positions,
  * keeps the fastest and reports it (any output pointer may be NULL);
  * bd_set_factor_config applies a known choice (e.g. from a cache).  Both drop
  * the captured step graph, which is rebuilt by the next bd_step.  Mixed
  * contexts only (BD_ERR_ARG otherwise); bd_tune_factor needs bd_set_state
  * first and synchronises the stream. */
 int bd_tune_factor(bd_ctx* ctx, int* panel_out, int* groups_out, double* ms_out, void* stream);
-int bd_set_factor_config(bd_ctx* ctx, int panel, int groups);
+int bd_set_factor_config(bd_ctx* ctx, int panel, int groups);  /* 1 <= panel <= 96 */
 
 /* Copy chain `chain`'s dense n x n (n = 3 N_c) matrix `which` to host FP64
  * row-major: which = 0 -> D, 1 -> the Cholesky factor B (zeros above the

@@ -1064,7 +1064,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
 }
 
 int bd_set_factor_config(bd_ctx* c, int panel, int groups) {
-  if (!c || !c->mixed || panel < 1 || panel > 16 || groups < 1 || groups > bd_ctx::kMaxGroups)
+  if (!c || !c->mixed || panel < 1 || panel > 96 || groups < 1 || groups > bd_ctx::kMaxGroups)
     return BD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   c->panel = panel;
@@ -1081,14 +1081,14 @@ int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, v
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int panels[] = {2, 4, 6, 8, 12};
+  const int panels[] = {2, 4, 6, 8, 12, 16, 24};
   const int groups[] = {1, 2, 4, 8, 12, 16};
   double best = 1e30;
   int bp = c->panel, bg = c->n_groups;
   int rc = BD_OK;
   for (int gi = 0; gi < 6 && rc == BD_OK; ++gi) {
     if (groups[gi] > c->n_chains) continue;
-    for (int pi = 0; pi < 5 && rc == BD_OK; ++pi) {
+    for (int pi = 0; pi < 7 && rc == BD_OK; ++pi) {
       c->panel = panels[pi];
       set_groups(c, groups[gi]);
       float tot = 0.f;

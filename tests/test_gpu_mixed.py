@@ -146,7 +146,7 @@ def test_factor_tuning_and_configs(bd, tmp_path):
     ctx = bd.Context(Nc, precision=bd.MIXED_TF32)
     ctx.set_state(cuda(r0))
     L = bd.lib()
-    for panel in (1, 2, 4, 6, 8, 12):
+    for panel in (1, 2, 4, 6, 8, 12, 16, 24):
         for groups in (1, 2, 4, 8):
             assert L.bd_set_factor_config(ctx._h, panel, groups) == 0
             ctx.assemble()
@@ -156,7 +156,7 @@ def test_factor_tuning_and_configs(bd, tmp_path):
             assert max(ctx.factor_residual(c) for c in (0, 6, 7)) < 2e-3
     cache = str(tmp_path / "tune.json")
     p, g, ms = ctx.tune_factor(cache)
-    assert p in (2, 4, 6, 8, 12) and g in (1, 2, 4, 8) and ms > 0
+    assert p in (2, 4, 6, 8, 12, 16, 24) and g in (1, 2, 4, 8) and ms > 0
     p2, g2, ms2 = ctx.tune_factor(cache)
     assert (p2, g2, ms2) == (p, g, None)
     ctx.step(cuda(inputs.gaussian_noise(2, int(Nc.sum()), 42)))
