@@ -36,6 +36,26 @@ METRIC = "chain-timesteps/s at N=1000 (mixed vs FP64, same GPU); Cholesky % tens
 UNIT = "chain-timesteps/s"
 
 
+def factor_tensor_peak(n, bf16_tflops):
+    """Tensor peak (TFLOP/s) of the mixed factorisation of chains of order n.
+
+    The panel solves multiply TF32 operands (0.5 x the bf16 rate, the nominal
+    1.1 / 2.25 PF ratio), the trailing updates FP16 ones (the bf16 rate).
+    With T = ceil(n / 128) tiles per chain the panel solves are T(T-1)/2 tile
+    products and the updates (T-1)T(T+1)/6; the peak is the flop-weighted
+    harmonic mean of the two rates.  Returns (peak, tf32 peak, TF32 share);
+    chains of a single tile have no tile products and get the TF32 peak.
+    """
+    tf32 = bf16_tflops * 0.5
+    T = np.ceil(np.asarray(n, np.float64) / 128.0)
+    trsm_tiles = float(np.sum(T * (T - 1) / 2))
+    upd_tiles = float(np.sum((T - 1) * T * (T + 1) / 6))
+    if trsm_tiles + upd_tiles == 0:
+        return tf32, tf32, 1.0
+    f_tf32 = trsm_tiles / (trsm_tiles + upd_tiles)
+    return 1.0 / (f_tf32 / tf32 + (1.0 - f_tf32) / bf16_tflops), tf32, f_tf32
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -195,17 +215,7 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "measured FP64 FMA throughput of this GPU (1.252 TFLOP/s)",
                 "kernel": "cholesky factorisation (FP64, CUDA cores)"}
     else:
-        # The panel solves multiply TF32 operands, the trailing updates FP16
-        # ones (twice the dense rate): the peak is the flop-weighted harmonic
-        # mean of the two, with the tile-level flop split of the blocked
-        # factorisation (128-wide tiles, T = padded order / 128 per chain).
-        tf32 = peaks["bf16_tflops"] * 0.5
-        f16 = peaks["bf16_tflops"]
-        T = np.ceil(n / 128.0)
-        trsm_tiles = float(np.sum(T * (T - 1) / 2))
-        upd_tiles = float(np.sum((T - 1) * T * (T + 1) / 6))
-        f_tf32 = trsm_tiles / (trsm_tiles + upd_tiles)
-        peak = 1.0 / (f_tf32 / tf32 + (1.0 - f_tf32) / f16)
+        peak, tf32, f_tf32 = factor_tensor_peak(n, peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved_tf, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"flop-weighted: panel solves TF32 = 0.5 x bf16 burst, trailing updates "
                                f"FP16 = bf16 burst ({peak_src}); TF32 share of the tile flops {f_tf32:.3f}",
