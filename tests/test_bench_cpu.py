@@ -52,3 +52,13 @@ def test_default_workload_peak():
     peak, tf32, f = bench.factor_tensor_peak(np.full(64, 3000.0), 1966.7)
     assert f == pytest.approx(276 / 2576, rel=1e-15)
     assert peak == pytest.approx(1776.374, rel=1e-6)
+
+
+def test_hbm_roofline():
+    # 64 chains of order 3000 in FP32: both triangles written by the assembly.
+    b = 64 * 3000.0 ** 2 * 4
+    r = bench.hbm_roofline(b, 0.372, 6694.5)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(b / 0.372e-3 / 1e9, rel=1e-15)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6694.5, rel=1e-15)
+    assert r["algorithmic_bytes_per_launch"] == b and r["ms_per_launch"] == 0.372
