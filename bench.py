@@ -64,6 +64,29 @@ def hbm_roofline(algorithmic_bytes, ms, hbm_gbs):
             "algorithmic_bytes_per_launch": algorithmic_bytes, "ms_per_launch": ms}
 
 
+def cpu_model() -> str:
+    """The host CPU's model string (x86 'model name', or the Arm implementer
+    and part numbers), for the record beside the oracle's timing."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return "unknown"
+    for line in info.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = part = None
+    for line in info.splitlines():
+        key = line.split(":", 1)[0].strip().lower()
+        if key == "cpu implementer" and impl is None:
+            impl = line.split(":", 1)[1].strip()
+        elif key == "cpu part" and part is None:
+            part = line.split(":", 1)[1].strip()
+    if impl or part:
+        return f"arm implementer {impl} part {part}"
+    return "unknown"
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -318,7 +341,8 @@ def cpu_baseline(w, Nc, r0, noise_host, max_chains):
     orc.run(p, Ns, rs, nz)
     el = time.perf_counter() - t0
     return {"value": S / el, "unit": UNIT, "cores": min(cores, S), "kind": "oracle",
-            "sample": f"{S} chains x 1 step of the workload (N={int(Nc.max())}), OpenMP over chains"}
+            "sample": f"{S} chains x 1 step of the workload (N={int(Nc.max())}), OpenMP over chains",
+            "host_cpus": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 def run_reference(args, rank, world):
@@ -348,7 +372,8 @@ def run_reference(args, rank, world):
             "config": {"workload": w.name, "n_chains_sampled": S, "n_beads": int(Nc.max()),
                        "hstar": w.hstar, "dt": w.dt, "Wi": w.Wi, "newton_tol": args.tol},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": min(cores, S), "kind": "oracle",
-                             "sample": f"{S} of {len(Nc)} chains per step, FP64 CPU oracle"},
+                             "sample": f"{S} of {len(Nc)} chains per step, FP64 CPU oracle",
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -62,3 +62,8 @@ def test_hbm_roofline():
     assert r["achieved"] == pytest.approx(b / 0.372e-3 / 1e9, rel=1e-15)
     assert r["frac"] == pytest.approx(r["achieved"] / 6694.5, rel=1e-15)
     assert r["algorithmic_bytes_per_launch"] == b and r["ms_per_launch"] == 0.372
+
+
+def test_cpu_model_is_a_string():
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m
