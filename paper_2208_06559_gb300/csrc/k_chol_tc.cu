@@ -14,13 +14,19 @@
 //   tc_gemm<UPDATE> : A_ij -= sum_{k0<=k<k1} L_ik L_jk^T for the trailing
 //              lower tiles (diagonal tiles: lower triangle only).
 //
-// The two products run on the 5th-generation tensor cores: TMA loads 128 x 32
-// FP32 slices of both operands (128-byte swizzle) into a 2-stage shared-memory
-// ring guarded by mbarriers (three CTAs per SM overlap each other's epilogues), one thread issues tcgen05.mma kind::tf32
-// (128 x 128 x 8) accumulating in TMEM, the four warps read TMEM back with
-// tcgen05.ld, stage the tile in shared memory in the same swizzled layout, and
-// one TMA reduce-add (update) or store (panel solve) writes it to the matrix.
-// Operands are TF32 (10-bit mantissa), accumulation FP32.  No multicast.
+// The two products run on the 5th-generation tensor cores.  TMA loads operand
+// slices (128-byte swizzle) into a 2-stage shared-memory ring guarded by
+// mbarriers (three CTAs per SM overlap each other's epilogues); one thread
+// issues the MMAs, accumulating in TMEM; the four warps read TMEM back with
+// tcgen05.ld and stage the tile in shared memory in the same swizzled layout.
+//   TRSM:   128 x 32 FP32 slices, rounded to nearest TF32 in shared memory,
+//           tcgen05.mma kind::tf32 (128 x 128 x 8).  The epilogue stores the
+//           TF32-rounded FP32 tile by TMA, then converts it to an FP16 copy
+//           (exact for |L| >= 2^-14: the same 10-bit mantissa, and |L| <= 1
+//           for D with a unit diagonal) stored by two more TMA stores.
+//   UPDATE: 128 x 64 FP16 slices of those copies, tcgen05.mma kind::f16
+//           (128 x 128 x 16), one TMA reduce-add into the FP32 matrix.
+// Accumulation is FP32 throughout.  No multicast.
 // All launches use programmatic dependent launch (pdl.h): a kernel's
 // prologue (barriers, TMEM allocation) overlaps the end of its predecessor.
 #include <cuda.h>
@@ -39,7 +45,7 @@ using namespace tc;
 
 constexpr int NB = kMixedTile;             // 128
 constexpr int kStages = 2;  // 2 x 32 KiB ring: three CTAs share an SM
-constexpr int kChunkBytes = NB * 32 * 4;   // 128 rows x 32 fp32 = 16 KiB
+constexpr int kChunkBytes = NB * 32 * 4;   // 128 rows x 32 fp32 (or 64 fp16) = 16 KiB
 constexpr int kStageBytes = 2 * kChunkBytes;
 constexpr int kTcSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
