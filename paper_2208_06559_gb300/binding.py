@@ -136,12 +136,39 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _f64(t, what: str, numel: int, device: Optional[int] = None, host_ok: bool = False):
+    """Check a tensor before its pointer goes to the library: float64,
+    contiguous, at least `numel` elements, and on the context's CUDA device
+    (or in host memory where the call accepts it).  The library sees only a
+    pointer, so a wrong element type or a short buffer would be read past its
+    end; this raises instead."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{what}: expected float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: the tensor must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{what}: {t.numel()} elements, {numel} needed")
+    if t.is_cuda:
+        if device is not None and t.device.index != device:
+            raise ValueError(f"{what}: tensor on cuda:{t.device.index}, context on cuda:{device}")
+    elif not host_ok:
+        raise ValueError(f"{what}: expected a CUDA tensor")
+    return t
+
+
 def mobility_apply_static(r, f, h_star: float = 0.25, a: float = 0.0, out=None, stream=None):
     """u = D(r) f for one chain through the allocation-free entry point
     (positions r and forces f: CUDA float64 [N, 3], N <= STATIC_MAX_BEADS)."""
     import torch
+    n = 3 * int(r.shape[0])
+    _f64(r, "mobility_apply_static: r", n)
+    _f64(f, "mobility_apply_static: f", n, device=r.device.index)
     if out is None:
         out = torch.empty_like(f)
+    _f64(out, "mobility_apply_static: out", n, device=r.device.index)
     _check(lib().bd_mobility_apply_static(_ptr(r), int(r.shape[0]), float(h_star), float(a),
                                           _ptr(f), _ptr(out), _stream(stream)),
            "bd_mobility_apply_static")
@@ -159,7 +186,10 @@ class Context:
                  flow: int = FLOW_NONE, Wi: float = 0.0, lam: float = 1.0, a: float = 0.0,
                  precision: int = FP64, tol: float = 1e-13, max_newton: int = 50,
                  refine: int = 1, constraint: int = RIGID, k_spring: float = 1e4):
+        import torch
         L = lib()
+        # the library's current device at creation (without CUDA, bd_create reports the error)
+        self.device = torch.cuda.current_device() if torch.cuda.is_available() else None
         self.n_beads = np.ascontiguousarray(np.asarray(n_beads, dtype=np.int32))
         self.n_chains = int(self.n_beads.shape[0])
         self.total_beads = int(self.n_beads.sum())
@@ -197,13 +227,14 @@ class Context:
 
     # -- state ---------------------------------------------------------
     def set_state(self, r, stream=None):
-        assert r.is_cuda and r.dtype.is_floating_point and r.is_contiguous()
+        _f64(r, "set_state", 3 * self.total_beads, self.device)
         _check(lib().bd_set_state(self._h, _ptr(r), _stream(stream)), "bd_set_state")
 
     def get_state(self, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty((self.total_beads, 3), dtype=torch.float64, device="cuda")
+            out = torch.empty((self.total_beads, 3), dtype=torch.float64, device=f"cuda:{self.device}")
+        _f64(out, "get_state", 3 * self.total_beads, self.device)
         _check(lib().bd_get_state(self._h, _ptr(out), _stream(stream)), "bd_get_state")
         return out
 
@@ -212,13 +243,14 @@ class Context:
         """Advance n_steps time steps with noise [n_steps, sum N, 3] (device or host)."""
         if n_steps is None:
             n_steps = int(noise.shape[0])
-        assert noise.is_contiguous() and noise.numel() >= n_steps * self.total_beads * 3
+        _f64(noise, "step: noise", int(n_steps) * self.total_beads * 3, self.device, host_ok=True)
         _check(lib().bd_step(self._h, int(n_steps), _ptr(noise), _stream(stream)), "bd_step")
 
     def observables(self, out=None, stream=None, with_status: bool = True):
         import torch
         if out is None:
-            out = torch.empty((self.n_chains, OBS_STRIDE), dtype=torch.float64, device="cuda")
+            out = torch.empty((self.n_chains, OBS_STRIDE), dtype=torch.float64, device=f"cuda:{self.device}")
+        _f64(out, "observables", self.n_chains * OBS_STRIDE, self.device)
         st = np.zeros(self.n_chains, dtype=np.int32) if with_status else None
         rc = lib().bd_observables(self._h, _ptr(out),
                                   st.ctypes.data_as(ctypes.c_void_p) if st is not None else None,
@@ -247,7 +279,7 @@ class Context:
         """One step launched kernel by kernel with stage-boundary events:
         {stage: ms}, keys PROFILE_STAGES (k_chain_end from the step start)."""
         import torch
-        assert noise.is_cuda and noise.is_contiguous()
+        _f64(noise, "profile_step: noise", 3 * self.total_beads, self.device)
         torch.cuda.synchronize()  # earlier work on other streams (e.g. set_state) is finished
         out = (ctypes.c_double * 8)()
         _check(lib().bd_profile_step(self._h, _ptr(noise), int(newton_iters), out), "bd_profile_step")
@@ -256,6 +288,10 @@ class Context:
     def adjoint(self, r0, noise, dJdr_final, ckpt_every: int = 20, stream=None):
         """(dJ/dWi, dJ/dh*) at fixed noise for J with gradient dJdr_final at the
         final positions; the context ends at the final state."""
+        n = 3 * self.total_beads
+        _f64(r0, "adjoint: r0", n, self.device)
+        _f64(noise, "adjoint: noise", int(noise.shape[0]) * n, self.device)
+        _f64(dJdr_final, "adjoint: dJdr_final", n, self.device)
         g = (ctypes.c_double * 2)()
         rc = lib().bd_adjoint(self._h, _ptr(r0), int(noise.shape[0]), _ptr(noise), int(ckpt_every),
                               _ptr(dJdr_final), g, _stream(stream))
@@ -304,12 +340,14 @@ class Context:
 
     def brownian(self, xi, stream=None):
         import torch
+        _f64(xi, "brownian: xi", 3 * self.total_beads, self.device)
         y = torch.empty_like(xi)
         _check(lib().bd_brownian(self._h, _ptr(xi), _ptr(y), _stream(stream)), "bd_brownian")
         return y
 
     def mobility_apply(self, f, stream=None):
         import torch
+        _f64(f, "mobility_apply: f", 3 * self.total_beads, self.device)
         u = torch.empty_like(f)
         _check(lib().bd_mobility_apply(self._h, _ptr(f), _ptr(u), _stream(stream)),
                "bd_mobility_apply")
@@ -317,7 +355,7 @@ class Context:
 
     def tensions(self, stream=None):
         import torch
-        T = torch.zeros(max(self.total_rods, 1), dtype=torch.float64, device="cuda")
+        T = torch.zeros(max(self.total_rods, 1), dtype=torch.float64, device=f"cuda:{self.device}")
         _check(lib().bd_get_tensions(self._h, _ptr(T), _stream(stream)), "bd_get_tensions")
         return T[: self.total_rods]
 

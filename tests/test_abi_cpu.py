@@ -86,3 +86,22 @@ def test_product_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "bd_oracle" not in txt, f
+
+
+def test_binding_checks_tensors_before_the_library_sees_them():
+    """The binding hands the library bare pointers, so it checks element type,
+    layout, size and placement first (no GPU needed: these all raise on the host)."""
+    import torch
+    from paper_2208_06559_gb300.binding import _f64
+    ok = torch.zeros((4, 3), dtype=torch.float64)
+    assert _f64(ok, "x", 12, host_ok=True) is ok
+    with pytest.raises(TypeError):
+        _f64(ok.numpy(), "x", 12, host_ok=True)
+    with pytest.raises(ValueError, match="float64"):
+        _f64(ok.float(), "x", 12, host_ok=True)
+    with pytest.raises(ValueError, match="contiguous"):
+        _f64(torch.zeros((3, 4), dtype=torch.float64).t(), "x", 12, host_ok=True)
+    with pytest.raises(ValueError, match="needed"):
+        _f64(ok, "x", 13, host_ok=True)
+    with pytest.raises(ValueError, match="CUDA"):
+        _f64(ok, "x", 12)
