@@ -250,7 +250,7 @@ class Context:
         import torch
         if out is None:
             out = torch.empty((self.n_chains, OBS_STRIDE), dtype=torch.float64, device=f"cuda:{self.device}")
-        _f64(out, "observables", self.n_chains * OBS_STRIDE, self.device)
+        _f64(out, "observables", self.n_chains * OBS_STRIDE, self.device, host_ok=True)
         st = np.zeros(self.n_chains, dtype=np.int32) if with_status else None
         rc = lib().bd_observables(self._h, _ptr(out),
                                   st.ctypes.data_as(ctypes.c_void_p) if st is not None else None,

@@ -105,3 +105,31 @@ def test_binding_checks_tensors_before_the_library_sees_them():
         _f64(ok, "x", 13, host_ok=True)
     with pytest.raises(ValueError, match="CUDA"):
         _f64(ok, "x", 12)
+
+
+def test_binding_host_buffers_where_the_library_copies(monkeypatch):
+    """bd_step and bd_observables take host memory (the library stages the
+    copy), so the binding lets host noise and a host observables buffer
+    through; positions must be on the device.  Run against a stub library:
+    only the binding's own checks are exercised."""
+    import torch
+    from paper_2208_06559_gb300 import binding
+
+    class _Stub:
+        def __getattr__(self, name):
+            return lambda *a, **k: b"stub" if name == "bd_strerror" else 0
+
+    monkeypatch.setattr(binding, "_lib", _Stub())
+    monkeypatch.setattr(binding, "_stream", lambda stream=None: ctypes.c_void_p(0))
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    ctx = binding.Context([5, 7])
+    noise = torch.zeros((2, 12, 3), dtype=torch.float64)
+    ctx.step(noise[0:1])
+    ctx.observables(out=torch.empty((2, binding.OBS_STRIDE), dtype=torch.float64), with_status=False)
+    with pytest.raises(ValueError, match="CUDA"):
+        ctx.set_state(torch.zeros((12, 3), dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        ctx.step(noise.float()[0:1])
+    with pytest.raises(ValueError, match="needed"):
+        ctx.step(noise[0:1], n_steps=2 + 1)
+    ctx._h = None
