@@ -58,6 +58,9 @@ def test_strerror_and_defaults(lib):
     lambda p, nb: setattr(p, "flow", 7),
     lambda p, nb: setattr(p, "precision", 9),
     lambda p, nb: nb.__setitem__(0, 1),   # a chain needs >= 2 beads
+    lambda p, nb: nb.__setitem__(1, 4097),  # past the per-chain kernel limit of 4096 beads
+    lambda p, nb: setattr(p, "dt", float("nan")),
+    lambda p, nb: setattr(p, "h_star", float("nan")),
     lambda p, nb: setattr(p, "constraint", 2),
     lambda p, nb: (setattr(p, "constraint", 1), setattr(p, "k_spring", 0.0)),  # Fraenkel needs K* > 0
 ])
