@@ -117,7 +117,8 @@ void bd_params_default(bd_params* p);
 
 /* Create a context on the current CUDA device: validates *p, copies n_beads,
  * allocates all device workspace.  *out receives the handle (NULL on error).
- * Errors: BD_ERR_ARG, BD_ERR_OOM, BD_ERR_CUDA. */
+ * Non-finite dt, h*, Wi, lambda or tol are rejected, as are the range errors
+ * noted on the fields above.  Errors: BD_ERR_ARG, BD_ERR_OOM, BD_ERR_CUDA. */
 int bd_create(const bd_params* p, bd_ctx** out);
 
 /* Free every resource of the context (NULL is allowed). */

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -579,6 +580,9 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   *out = nullptr;
   if (!p || p->n_chains < 1 || !p->n_beads) return BD_ERR_ARG;
   if (!(p->dt > 0.0) || !(p->h_star >= 0.0)) return BD_ERR_ARG;
+  if (!std::isfinite(p->dt) || !std::isfinite(p->h_star) || !std::isfinite(p->Wi) ||
+      !std::isfinite(p->lambda) || !std::isfinite(p->tol))
+    return BD_ERR_ARG;
   const double a = p->a > 0.0 ? p->a : p->h_star;
   if (p->h_star > 0.0 && a < p->h_star) return BD_ERR_ARG;  // D may not be positive definite
   if (p->flow < BD_FLOW_NONE || p->flow > BD_FLOW_UNIAXIAL) return BD_ERR_ARG;

@@ -61,6 +61,10 @@ def test_strerror_and_defaults(lib):
     lambda p, nb: nb.__setitem__(1, 4097),  # past the per-chain kernel limit of 4096 beads
     lambda p, nb: setattr(p, "dt", float("nan")),
     lambda p, nb: setattr(p, "h_star", float("nan")),
+    lambda p, nb: setattr(p, "dt", float("inf")),
+    lambda p, nb: setattr(p, "Wi", float("nan")),
+    lambda p, nb: setattr(p, "lambda_", float("inf")),
+    lambda p, nb: setattr(p, "tol", float("nan")),
     lambda p, nb: setattr(p, "constraint", 2),
     lambda p, nb: (setattr(p, "constraint", 1), setattr(p, "k_spring", 0.0)),  # Fraenkel needs K* > 0
 ])
