@@ -307,8 +307,11 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if prec == bd.FP64 else
-                     "f32 storage, tf32/f16 tensor-core products, f32 diagonal tiles, f64-accurate tension solve",
+            "dtype": "f64" if prec == bd.FP64 else "f32",
+            "dtype_detail": "f64 throughout" if prec == bd.FP64 else
+                            "f32 storage and arithmetic; tf32 (panel solves) and f16 (trailing updates) "
+                            "tensor-core operands with f32 accumulation; f32 diagonal tiles; "
+                            "double-float (f64-accurate) tension-solve products",
             "data": "synthetic (seeded random-walk chains, N(0,1) noise)",
             "config": {"workload": w.name, "n_chains_per_gpu": len(Nc), "n_beads": int(Nc.max()),
                        "hstar": w.hstar, "a": w.hstar, "dt": w.dt,
