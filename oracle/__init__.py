@@ -29,6 +29,7 @@ ERR_NOT_PD = -4
 ERR_CONSTRAINT = -5
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
 RIGID, FRAENKEL = 0, 1
+SCHEME_MIDPOINT, SCHEME_EULER = 0, 1
 OBS_STRIDE = 12
 
 
@@ -44,13 +45,16 @@ class Params(ctypes.Structure):
         ("max_newton", ctypes.c_int),
         ("constraint", ctypes.c_int),
         ("kspring", ctypes.c_double),
+        ("scheme", ctypes.c_int),
     ]
 
 
 def make_params(hstar=0.25, a=0.0, dt=1e-4, flow=FLOW_NONE, Wi=0.0, lam=1.0,
-                tol=1e-13, max_newton=50, constraint=RIGID, kspring=0.0) -> Params:
+                tol=1e-13, max_newton=50, constraint=RIGID, kspring=0.0,
+                scheme=SCHEME_MIDPOINT) -> Params:
     return Params(float(hstar), float(a), float(dt), int(flow), float(Wi),
-                  float(lam), float(tol), int(max_newton), int(constraint), float(kspring))
+                  float(lam), float(tol), int(max_newton), int(constraint), float(kspring),
+                  int(scheme))
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +83,8 @@ def lib():
         L.or_cholesky.restype = ctypes.c_int
         L.or_trmv_lower.argtypes = [ctypes.c_int, dp, dp, dp]
         L.or_gemv.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_trsv_lower_t.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_tangent_project.argtypes = [ctypes.c_int, dp, dp, dp]
         L.or_kappa.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         L.or_factor_residual.argtypes = [ctypes.c_int, dp, dp]
         L.or_factor_residual.restype = ctypes.c_double
@@ -141,6 +147,25 @@ def trmv_lower(L, x):
     y = np.zeros_like(x)
     lib().or_trmv_lower(L.shape[0], _d(L), _d(x), _d(y))
     return y
+
+
+def trsv_lower_t(L, x):
+    """z = L^{-T} x (back substitution with the transpose of lower-triangular L)."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    z = np.zeros_like(x)
+    lib().or_trsv_lower_t(L.shape[0], _d(L), _d(x), _d(z))
+    return z
+
+
+def tangent_project(r, y):
+    """Orthogonal projection of a bead displacement y onto the tangent space of
+    the rod constraints |Q_k| = 1 at positions r."""
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros_like(y)
+    lib().or_tangent_project(r.shape[0], _d(r), _d(y), _d(out))
+    return out
 
 
 def gemv(A, x):

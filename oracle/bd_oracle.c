@@ -104,6 +104,58 @@ void or_trmv_lower(int n, const double* L, const double* x, double* y) {
   }
 }
 
+void or_trsv_lower_t(int n, const double* L, const double* x, double* z) {
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int j = i + 1; j < n; ++j) s -= L[(size_t)j * n + i] * z[j];
+    z[i] = s / L[(size_t)i * n + i];
+  }
+}
+
+static int lu_solve(int m, double* A, double* b);
+
+void or_tangent_project(int N, const double* r, const double* y, double* out) {
+  int m = N - 1;
+  double* u = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+  double* H = (double*)calloc((size_t)(m > 0 ? m : 1) * (m > 0 ? m : 1), sizeof(double));
+  double* c = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  for (int k = 0; k < m; ++k) {
+    double q[3], qn = 0.0;
+    for (int e = 0; e < 3; ++e) {
+      q[e] = r[3 * (k + 1) + e] - r[3 * k + e];
+      qn += q[e] * q[e];
+    }
+    qn = sqrt(qn);
+    for (int e = 0; e < 3; ++e) u[3 * k + e] = q[e] / qn;
+  }
+  /* H = A A^T and c = A y, row k of A being (-u_k at bead k, +u_k at bead k+1) */
+  for (int k = 0; k < m; ++k) {
+    c[k] = 0.0;
+    for (int e = 0; e < 3; ++e) c[k] += u[3 * k + e] * (y[3 * (k + 1) + e] - y[3 * k + e]);
+    for (int l = 0; l < m; ++l) {
+      double s = 0.0;
+      for (int i = 0; i < N; ++i)
+        for (int e = 0; e < 3; ++e) {
+          double ak = (i == k + 1 ? u[3 * k + e] : 0.0) - (i == k ? u[3 * k + e] : 0.0);
+          double al = (i == l + 1 ? u[3 * l + e] : 0.0) - (i == l ? u[3 * l + e] : 0.0);
+          s += ak * al;
+        }
+      H[(size_t)k * m + l] = s;
+    }
+  }
+  if (m > 0) lu_solve(m, H, c); /* c <- (A A^T)^{-1} A y */
+  for (int i = 0; i < N; ++i)
+    for (int e = 0; e < 3; ++e) {
+      double s = y[3 * i + e];
+      if (i < m) s += c[i] * u[3 * i + e];             /* row i of A: -u_i at bead i */
+      if (i > 0) s -= c[i - 1] * u[3 * (i - 1) + e];   /* row i-1: +u_{i-1} at bead i */
+      out[3 * i + e] = s;
+    }
+  free(u);
+  free(H);
+  free(c);
+}
+
 void or_gemv(int n, const double* A, const double* x, double* y) {
   for (int i = 0; i < n; ++i) {
     double s = 0.0;
@@ -274,6 +326,10 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
   double* rn = (double*)malloc(sizeof(double) * n);
   double* u = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
   double* T = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double* z = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* rm = (double*)malloc(sizeof(double) * n);
+  double* Dm = (double*)malloc(sizeof(double) * (size_t)n * n);
   int status;
 
   /* 1. diffusion tensor at the current positions, Eqs. (7)-(9) */
@@ -311,10 +367,33 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
       free(rn);
       free(u);
       free(T);
+      free(z);
+      free(w);
+      free(rm);
+      free(Dm);
       return OR_OK;
     }
-    /* 4. predictor r* = r + dt kappa.r + y (Eq. (6) flow term) and the old
-     *    rod directions u_k = Q_k / |Q_k| along which tensions act */
+    /* 4. The mobility and the rod directions the step uses.  Euler: those
+     *    of r.  Midpoint (a reading: the paper runs stiff springs, whose
+     *    statistics need no such term): they are taken at
+     *    r_m = r + P y / 2, P the orthogonal projection onto the tangent
+     *    space of the constraints at r, and the Brownian displacement
+     *    becomes sqrt(2 dt) D_m z with z = L^{-T} xi (D z = L xi).  Through
+     *    the correlation of r_m with z this adds the mean drift that the
+     *    rigid-rod diffusion on the constraint surface needs with HI. */
+    const double* Dstep = D;
+    const double* rdir = r;
+    if (p->scheme != OR_SCHEME_EULER) {
+      or_trsv_lower_t(n, L, xi, z);
+      or_tangent_project(N, r, y, w);
+      for (int e = 0; e < n; ++e) rm[e] = r[e] + 0.5 * s * w[e];
+      or_assemble(N, rm, p->hstar, a, Dm);
+      or_gemv(n, Dm, z, y); /* y <- D_m z */
+      Dstep = Dm;
+      rdir = rm;
+    }
+    /* 5. predictor r* = r + dt kappa.r + sqrt(2 dt) y (Eq. (6) flow term)
+     *    and the rod directions u_k = Q_k / |Q_k| along which tensions act */
     for (int i = 0; i < N; ++i)
       for (int k = 0; k < 3; ++k) {
         double kr = kap[3 * k] * r[3 * i] + kap[3 * k + 1] * r[3 * i + 1] +
@@ -324,15 +403,15 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
     for (int k = 0; k < m; ++k) {
       double q[3], qn = 0.0;
       for (int c = 0; c < 3; ++c) {
-        q[c] = r[3 * (k + 1) + c] - r[3 * k + c];
+        q[c] = rdir[3 * (k + 1) + c] - rdir[3 * k + c];
         qn += q[c] * q[c];
       }
       qn = sqrt(qn);
       for (int c = 0; c < 3; ++c) u[3 * k + c] = q[c] / qn;
     }
-    /* 5. rod tensions with |Q_k| = 1; 6. r <- r(T) */
+    /* 6. rod tensions with |Q_k| = 1; 7. r <- r(T) */
     int it = 0;
-    status = or_tension_solve(N, D, rs, u, p->dt, p->tol, p->max_newton, T, rn, &it);
+    status = or_tension_solve(N, Dstep, rs, u, p->dt, p->tol, p->max_newton, T, rn, &it);
     if (iters) *iters = it;
     if (status == OR_OK) {
       memcpy(r, rn, sizeof(double) * n);
@@ -359,6 +438,10 @@ int or_step(const or_params* p, int N, double* r, const double* xi,
   free(rn);
   free(u);
   free(T);
+  free(z);
+  free(w);
+  free(rm);
+  free(Dm);
   return status;
 }
 

@@ -38,6 +38,9 @@ extern "C" {
 #define OR_RIGID 0    /* rigid rods: tension solve */
 #define OR_FRAENKEL 1 /* Fraenkel springs of stiffness kspring, semi-implicit (Sec. 3) */
 
+#define OR_SCHEME_MIDPOINT 0 /* rigid rods: midpoint corrector (the default) */
+#define OR_SCHEME_EULER 1    /* rigid rods: one projection from the start of the step */
+
 #define OR_OBS_STRIDE 12 /* Rx Ry Rz R2 Rg2 stretch max||Q|-1| newton_iters tau_xx tau_yy tau_zz tau_xy */
 
 typedef struct {
@@ -51,6 +54,7 @@ typedef struct {
   int max_newton;  /* Newton update cap */
   int constraint;  /* OR_RIGID or OR_FRAENKEL */
   double kspring;  /* Fraenkel spring constant K* (OR_FRAENKEL) */
+  int scheme;      /* OR_SCHEME_* (rigid rods only) */
 } or_params;
 
 /* 3x3 RPY block for separation R = r_i - r_j, Sec. 3 Eqs. (8)-(9). */
@@ -62,6 +66,13 @@ void or_assemble(int N, const double* r, double hstar, double a, double* D);
 int or_cholesky(int n, const double* D, double* L);
 /* y = L x with L lower triangular (the sum over j <= i of Eq. (6)). */
 void or_trmv_lower(int n, const double* L, const double* x, double* y);
+/* z = L^{-T} x: back substitution with the transpose of lower-triangular L. */
+void or_trsv_lower_t(int n, const double* L, const double* x, double* z);
+/* out = y - A^T (A A^T)^{-1} A y: the orthogonal projection of a bead
+ * displacement y ([N][3]) onto the tangent space of the rod constraints
+ * |Q_k| = 1 at positions r.  Row k of A holds -u_k at bead k and +u_k at
+ * bead k+1 (u_k = Q_k/|Q_k|). */
+void or_tangent_project(int N, const double* r, const double* y, double* out);
 /* y = A x, dense. */
 void or_gemv(int n, const double* A, const double* x, double* y);
 /* kappa for the flow type (Sec. 3, flow-force paragraph); row-major 3x3. */
@@ -87,7 +98,12 @@ void or_fraenkel_update(int N, const double* D, const double* kappa, double dt, 
                         const double* r, const double* y, double* r_new, double* T_out);
 
 /* One full time step for one chain (assembly, Cholesky, Brownian
- * displacement, flow predictor, tension solve or Fraenkel update).  r is updated in place
+ * displacement, flow predictor, tension solve or Fraenkel update).
+ * Rigid rods, OR_SCHEME_MIDPOINT: with y = sqrt(2 dt) L xi and z = L^{-T} xi
+ * (so that D z = L xi), the midpoint r_m = r + P y / 2 (P: or_tangent_project
+ * at r), D_m = D(r_m) and the rod directions u_m of r_m; the predictor is
+ * r* = r + dt kappa.r + sqrt(2 dt) D_m z and the tensions act along u_m
+ * through D_m.  OR_SCHEME_EULER: D and u of r throughout.  r is updated in place
  * unless the step fails, in which case r is left unchanged.
  * T_out (N-1) may be NULL.  Returns 0 or an error code. */
 int or_step(const or_params* p, int N, double* r, const double* xi,

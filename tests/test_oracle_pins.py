@@ -302,6 +302,126 @@ def test_newton_cap_reports_failure():
     assert st == orc.ERR_CONSTRAINT
 
 
+# --------------------------------------------- midpoint scheme (rigid rods)
+def test_trsv_lower_t_brute_force():
+    """z = L^{-T} x against numpy's general solve of L^T z = x."""
+    g = inputs.rng(6)
+    for n in (1, 2, 5, 48):
+        L = np.tril(g.standard_normal((n, n))) + 4 * np.eye(n)
+        x = g.standard_normal(n)
+        np.testing.assert_allclose(orc.trsv_lower_t(L, x), np.linalg.solve(L.T, x),
+                                   rtol=1e-13, atol=1e-13)
+
+
+def _constraint_rows(r):
+    """Rows of A: -u_k at bead k, +u_k at bead k+1."""
+    N = r.shape[0]
+    Q = np.diff(r, axis=0)
+    u = Q / np.linalg.norm(Q, axis=1)[:, None]
+    A = np.zeros((N - 1, 3 * N))
+    for k in range(N - 1):
+        A[k, 3 * k:3 * k + 3] = -u[k]
+        A[k, 3 * k + 3:3 * k + 6] = u[k]
+    return A
+
+
+def test_tangent_projection_properties():
+    """P y keeps every rod's length to first order (A P y = 0), is idempotent,
+    and y - P y is normal to the tangent space (spanned by the rows of A);
+    for a dumbbell P y removes the relative motion along the rod."""
+    g = inputs.rng(7)
+    for N in (2, 3, 9):
+        r = inputs.random_walk([N], 70 + N)
+        y = g.standard_normal((N, 3))
+        Py = orc.tangent_project(r, y)
+        A = _constraint_rows(r)
+        assert np.abs(A @ Py.ravel()).max() < 1e-13
+        np.testing.assert_allclose(orc.tangent_project(r, Py), Py, atol=1e-13)
+        d = (y - Py).ravel()
+        coef = np.linalg.lstsq(A.T, d, rcond=None)[0]
+        np.testing.assert_allclose(A.T @ coef, d, atol=1e-13)
+    r = np.array([[0.0, 0, 0], [0.0, 0.6, 0.8]])
+    u = r[1] - r[0]
+    y = np.array([[0.3, -0.2, 0.5], [0.1, 0.4, -0.7]])
+    s = u @ (y[1] - y[0]) / 2
+    np.testing.assert_allclose(orc.tangent_project(r, y), y + s * np.array([u, -u]), atol=1e-15)
+
+
+def _step_drift(p, r):
+    """Mean of (r_new - r)/dt over xi ~ N(0, I), to O(dt): with noise +xi and
+    -xi the odd orders cancel, and the expectation of the remaining quadratic
+    form in xi is its value at 0 plus the sum of its unit-vector terms."""
+    n = r.size
+
+    def g2(xi):
+        a = orc.step(p, r, xi.reshape(-1, 3))
+        b = orc.step(p, r, -xi.reshape(-1, 3))
+        assert a[2] == 0 and b[2] == 0
+        return (a[0] + b[0] - 2 * r).ravel() / (2 * p.dt)
+
+    c = g2(np.zeros(n))
+    tot = c.copy()
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        tot += g2(e) - c
+    return tot
+
+
+def _rigid_drift_tangent(r, hs, a, kap):
+    """Tangent part of the drift of rigid-rod diffusion with HI on the
+    constraint surface (equilibrium weight uniform in the surface measure):
+    P (kappa r) + P_S sum_ij (P_S)_ij d_j (D_c)_{. i}, with the constrained
+    mobility D_c = P D, P = I - D A^T (A D A^T)^{-1} A (flow velocity with the
+    constraint forces that hold the rods) and P_S the orthogonal projector
+    onto the tangent space; derivatives by central differences of D_c."""
+    N = r.shape[0]
+    n = 3 * N
+
+    def Dc(x):
+        x = x.reshape(N, 3)
+        D = orc.assemble(x, hs, a)
+        A = _constraint_rows(x)
+        return D - D @ A.T @ np.linalg.solve(A @ D @ A.T, A @ D)
+
+    A = _constraint_rows(r)
+    D = orc.assemble(r, hs, a)
+    P = np.eye(n) - D @ A.T @ np.linalg.solve(A @ D @ A.T, A)
+    PS = np.eye(n) - A.T @ np.linalg.solve(A @ A.T, A)
+    h = 1e-5
+    div = np.zeros(n)
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        dD = (Dc(r.ravel() + e) - Dc(r.ravel() - e)) / (2 * h)
+        div += dD @ PS[:, j]          # sum_i dD[:, i] PS[i, j]
+    v = (r @ kap.T).ravel()
+    return P @ v + PS @ div
+
+
+@pytest.mark.parametrize("N,hs,a,flow", [(3, 0.25, 0.25, orc.FLOW_NONE), (5, 0.25, 0.25, orc.FLOW_UNIAXIAL),
+                                         (4, 0.25, 0.4, orc.FLOW_SHEAR), (4, 0.5, 0.5, orc.FLOW_NONE),
+                                         (4, 0.0, 0.25, orc.FLOW_NONE)])
+def test_midpoint_step_has_the_rigid_rod_drift(N, hs, a, flow):
+    """The step's mean displacement per unit time, projected on the tangent
+    space, equals the drift of rigid-rod diffusion with HI; the Euler
+    projection misses its HI part (equal only at h* = 0)."""
+    r = inputs.random_walk([N], 200 + N)
+    Wi = 2.0 if flow != orc.FLOW_NONE else 0.0
+    want = _rigid_drift_tangent(r, hs, a, orc.kappa(flow, Wi))
+    A = _constraint_rows(r)
+    PS = np.eye(3 * N) - A.T @ np.linalg.solve(A @ A.T, A)
+    p = orc.make_params(hstar=hs, a=a, dt=1e-6, flow=flow, Wi=Wi, tol=1e-14)
+    got = PS @ _step_drift(p, r)
+    np.testing.assert_allclose(got, want, atol=2e-4 * max(1.0, np.abs(want).max()))
+    pe = orc.make_params(hstar=hs, a=a, dt=1e-6, flow=flow, Wi=Wi, tol=1e-14, scheme=orc.SCHEME_EULER)
+    gap = np.abs(PS @ _step_drift(pe, r) - want).max()
+    if hs > 0:
+        assert gap > 1e-2
+    else:
+        assert gap < 2e-4
+
+
 # -------------------------------------------------------------- dynamics
 def test_rod_lengths_held_over_many_steps():
     Nc = np.array([16, 33, 5], np.int32)
@@ -351,8 +471,9 @@ def test_dumbbell_rotational_diffusion():
             assert abs(c.mean() - np.exp(-rate * t_end)) < 3 * se + 0.01, (hs, t_end, c.mean())
 
 
-def _equilibrium_samples(N, hs, n_chains, dt, t_burn, n_samp, t_gap, seed):
-    p = orc.make_params(hstar=hs, a=0.25, dt=dt, tol=1e-12)
+def _equilibrium_samples(N, hs, n_chains, dt, t_burn, n_samp, t_gap, seed,
+                         scheme=orc.SCHEME_MIDPOINT):
+    p = orc.make_params(hstar=hs, a=0.25, dt=dt, tol=1e-12, scheme=scheme)
     Nc = np.full(n_chains, N, np.int32)
     r = inputs.random_walk(Nc, seed, stretched=True)
     k = seed + 1
@@ -395,25 +516,55 @@ def test_equilibrium_statics_free_draining():
 
 
 @pytest.mark.slow
-def test_equilibrium_statics_with_hi_bounded():
-    """With h* = 0.25 the rigid projection scheme (no HI-dependent metric
-    drift) shifts <R^2> by a few percent at N = 4; the shift stays below 5 %.
-    The 3-s.e. equality is checked in the strict test below (expected to fail
-    at this sample size)."""
+def test_equilibrium_statics_euler_scheme_is_biased_with_hi():
+    """The Euler projection (mobility and rod directions of the start of the
+    step) lacks the HI part of the rigid-rod drift: at N = 4, h* = 0.25 it
+    shifts <R^2> by a few percent.  The shift stays below 5 %."""
     N = 4
-    R2, Rg2, cs = _equilibrium_samples(N, 0.25, 1500, 1e-3, 3.0, 8, 0.5, 80)
+    R2, Rg2, cs = _equilibrium_samples(N, 0.25, 1500, 1e-3, 3.0, 8, 0.5, 80, orc.SCHEME_EULER)
     assert abs(R2.mean() / (N - 1) - 1) < 0.05
     assert abs(cs.mean()) < 0.05
 
 
 @pytest.mark.slow
-@pytest.mark.xfail(strict=False, reason="rigid projection without the HI metric drift biases "
-                   "<R^2> by about -2.4 % at N = 4, h* = 0.25 (4 s.e. at 2000 chains)")
 def test_equilibrium_statics_with_hi_strict():
+    """Midpoint scheme, h* = 0.25: <R^2> = (N - 1) b^2, <Rg^2> = b^2 (N^2-1)/(6N)
+    and <u_k . u_k+1> = 0, each within 3 s.e. (HI leaves the statics unchanged)."""
     N = 4
     R2, Rg2, cs = _equilibrium_samples(N, 0.25, 1500, 1e-3, 3.0, 8, 0.5, 90)
     assert abs(R2.mean() - (N - 1)) < 3 * _se(R2)
+    assert abs(Rg2.mean() - (N * N - 1) / (6 * N)) < 3 * _se(Rg2)
     assert abs(cs.mean()) < 3 * _se(cs)
+
+
+# <cos^2> of the bond angle of a rigid trimer.  Rigid constraints weight a
+# conformation by sqrt(det G), G = A A^T the Gram matrix of the constraint
+# gradients (2 on the diagonal, -cos(theta) off it), relative to the freely
+# jointed measure: sqrt(4 - c^2) for a trimer, c = cos(theta).  Then
+# <c^2> = int c^2 sqrt(4-c^2) dc / int sqrt(4-c^2) dc over [-1, 1]
+#       = (pi/3 - sqrt(3)/4) / (sqrt(3)/2 + pi/3) = 0.32104...,
+# against 1/3 for stiff springs (uniform c).
+RIGID_TRIMER_COS2 = (np.pi / 3 - np.sqrt(3) / 4) / (np.sqrt(3) / 2 + np.pi / 3)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("hs", [0.0, 0.25])
+def test_rigid_trimer_bond_angle(hs):
+    """<cos^2 theta> of a rigid trimer is the metric-weighted 0.3210, not the
+    1/3 of stiff springs, with and without HI, within 3 s.e."""
+    n = 2000
+    p = orc.make_params(hstar=hs, a=0.25, dt=1e-3, tol=1e-12)
+    Nc = np.full(n, 3, np.int32)
+    r = inputs.random_walk(Nc, 93, stretched=True)
+    r, *_ = orc.run(p, Nc, r, inputs.gaussian_noise(3000, 3 * n, 94))
+    c2 = []
+    for k in range(8):
+        r, _, st, _, _ = orc.run(p, Nc, r, inputs.gaussian_noise(500, 3 * n, 95 + k))
+        assert np.all(st == 0)
+        Q = np.diff(r.reshape(n, 3, 3), axis=1)
+        c2.append(((Q[:, 0] * Q[:, 1]).sum(1)) ** 2)
+    c2 = np.mean(c2, axis=0)
+    assert abs(c2.mean() - RIGID_TRIMER_COS2) < 3 * _se(c2), (c2.mean(), _se(c2))
 
 
 def test_observables_closed_forms():
