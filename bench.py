@@ -166,8 +166,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     prec = {"fp64": bd.FP64, "tf32": bd.MIXED_TF32}[args.precision] if args.precision else \
         (bd.MIXED_TF32 if w.precision != 0 else bd.FP64)
+    scheme = {"midpoint": bd.SCHEME_MIDPOINT, "euler": bd.SCHEME_EULER}[args.scheme]
     kw = dict(h_star=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol, constraint=w.constraint,
-              k_spring=w.kspring)
+              k_spring=w.kspring, scheme=scheme)
 
     def barrier():
         if world > 1:
@@ -298,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        cpu = cpu_baseline(w, Nc, r0_host, noise_host, args.cpu_chains)
+        cpu = cpu_baseline(w, Nc, r0_host, noise_host, args.cpu_chains, args.scheme)
 
     if rank == 0:
         tile = 32 if prec == bd.FP64 else 128
@@ -318,6 +319,7 @@ def run_ours(args, rank, world, local_rank):
                        "flow": ["none", "shear", "uniaxial"][w.flow], "Wi": w.Wi, "lambda": 1.0,
                        "newton_tol": args.tol,
                        "constraint": ["rigid", "fraenkel"][w.constraint],
+                       **({"scheme": args.scheme} if w.constraint == 0 else {}),
                        **({"k_spring": w.kspring} if w.constraint == 1 else {}),
                        "precision": "fp64" if prec == bd.FP64 else "mixed_tf32_refined",
                        "l2": f"inputs larger than L2 (per-step matrices {mat_gb:.1f} GB)",
@@ -331,12 +333,12 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
-def cpu_baseline(w, Nc, r0, noise_host, max_chains):
+def cpu_baseline(w, Nc, r0, noise_host, max_chains, scheme="midpoint"):
     import oracle as orc
     cores = orc.num_threads()
     S = int(min(len(Nc), max(1, min(cores, max_chains))))
     p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, constraint=w.constraint,
-                        kspring=w.kspring)
+                        kspring=w.kspring, scheme=0 if scheme == "midpoint" else 1)
     Ns = Nc[:S]
     rs = r0[: int(Ns.sum())]
     nz = np.ascontiguousarray(noise_host[:1, : int(Ns.sum())])
@@ -360,7 +362,8 @@ def run_reference(args, rank, world):
     r = inputs.random_walk(Ns, w.seed)
     noise = inputs.gaussian_noise(args.steps + args.warmup, int(Ns.sum()), w.seed + 1)
     p = orc.make_params(hstar=w.hstar, dt=w.dt, flow=w.flow, Wi=w.Wi, tol=args.tol,
-                        constraint=w.constraint, kspring=w.kspring)
+                        constraint=w.constraint, kspring=w.kspring,
+                        scheme=0 if args.scheme == "midpoint" else 1)
     for i in range(args.warmup):
         r, *_ = orc.run(p, Ns, r, noise[i:i + 1])
     t0 = time.perf_counter()
@@ -390,6 +393,8 @@ def main():
     ap.add_argument("--workload", default="n1000x64_mixed_shear", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32"])
     ap.add_argument("--tol", type=float, default=1e-13)
+    ap.add_argument("--scheme", default="midpoint", choices=["midpoint", "euler"],
+                    help="rigid-rod step: midpoint corrector (default) or the Euler projection")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-chains", type=int, default=16)

@@ -16,6 +16,15 @@
  *      Fraenkel springs (Sec. 3 Eq. (3), eqQ2, Eqs. (23)-(25)): steps 1-3, one
  *      mobility product with the spring forces at t, then a closed-form
  *      update per link.
+ * Rigid rods with BD_SCHEME_MIDPOINT (the default) evaluate the mobility of
+ * steps 3-5 and the rod directions of step 5 at the midpoint
+ * r_m = r + P y / 2 (y = sqrt(2 dt) L xi, P the orthogonal projection onto
+ * the tangent space of the rod constraints at r) and move by
+ * sqrt(2 dt) D(r_m) L^{-T} xi: one Cholesky factor per step, and the mean
+ * drift of rigid-rod diffusion with HI, whose statics HI leaves unchanged.
+ * BD_SCHEME_EULER uses D and the rod directions of r throughout; with
+ * h* > 0 it lacks part of that drift (the paper itself runs stiff springs,
+ * which need no such term).
  *
  * Conventions.  A chain has N >= 2 beads and N-1 rods; rod k joins bead k to
  * bead k+1.  Rod length b = 1 and bead mobility kT/zeta = 1, so D_ii = I.
@@ -69,12 +78,14 @@ typedef enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2 } bd_fl
  * mantissa; |L_ij| <= 1 since D has a unit diagonal), FP32 accumulation;
  * one refinement step on the Brownian displacement; the tension iteration
  * with FP64-level (double-float) products, so rods hold to the tolerance.
- * BD_MIXED_BF16: accepted and run exactly as BD_MIXED_TF32.  FP16 operands
+ * BD_MIXED_BF16: rejected by bd_create with BD_ERR_ARG (no factorisation
+ * with BF16 operands is built).  The FP16 operands of BD_MIXED_TF32 already
  * run at the BF16 tensor rate with two more mantissa bits; BF16 operands
  * (8-bit mantissa) leave the refined factor's error at 4.6e-6 for N = 1000
  * in an FP64 emulation of the factorisation's roundings, above 1e-6. */
 typedef enum { BD_FP64 = 0, BD_MIXED_TF32 = 1, BD_MIXED_BF16 = 2 } bd_precision;
 typedef enum { BD_RIGID = 0, BD_FRAENKEL = 1 } bd_constraint;
+typedef enum { BD_SCHEME_MIDPOINT = 0, BD_SCHEME_EULER = 1 } bd_scheme;
 
 /* Observables written per chain by bd_observables (Sec. 5 Eqs. (25)-(29)). */
 #define BD_OBS_STRIDE 12
@@ -102,17 +113,18 @@ typedef struct {
   int flow;              /* bd_flow */
   double Wi;             /* Weissenberg number; rate = Wi / lambda */
   double lambda;         /* relaxation time; <= 0 means 1 */
-  int precision;         /* bd_precision */
+  int precision;         /* bd_precision: BD_FP64 or BD_MIXED_TF32 */
   int constraint;        /* bd_constraint: BD_RIGID (tension solve) or BD_FRAENKEL */
   double tol;            /* Newton tolerance on max_k | |Q_k|^2 - 1 |; <= 0 -> 1e-13 */
   int max_newton;        /* Newton update cap; <= 0 -> 50 */
   int refine;            /* mixed precision: 1 = one refinement step on B xi */
   double k_spring;       /* BD_FRAENKEL: spring constant K* > 0 (Eq. (3)); unused for BD_RIGID */
+  int scheme;            /* bd_scheme of the rigid-rod step (BD_RIGID only) */
 } bd_params;
 
 /* Fill *p with defaults: 1 chain (n_beads NULL), h* = 0.25, a = h*, dt = 1e-4,
  * no flow, lambda = 1, BD_FP64, BD_RIGID, tol 1e-13, max_newton 50, refine 1,
- * k_spring 1e4. */
+ * k_spring 1e4, BD_SCHEME_MIDPOINT. */
 void bd_params_default(bd_params* p);
 
 /* Create a context on the current CUDA device: validates *p, copies n_beads,
@@ -188,6 +200,15 @@ int bd_brownian(bd_ctx* ctx, const double* xi_dev, double* y_dev, void* stream);
 int bd_mobility_apply(bd_ctx* ctx, const double* f_dev, double* u_dev, void* stream);
 /* Stage 5 input/outputs: tensions of the last step, [sum (N-1)] FP64. */
 int bd_get_tensions(bd_ctx* ctx, double* T_dev, void* stream);
+/* Stage 3' of the midpoint scheme (after bd_assemble and bd_factor; rigid
+ * contexts with BD_SCHEME_MIDPOINT only): for xi [sum N][3] (device),
+ * rmid_dev [sum N][3] receives r_m = r + P y / 2 (y = sqrt(2 dt) B xi, P the
+ * orthogonal projection onto the tangent space of |Q_k| = 1 at r) and y_dev
+ * [sum N][3] the step's Brownian displacement sqrt(2 dt) D(r_m) B^{-T} xi.
+ * Mixed precision: y is the refined displacement of stage 3 plus
+ * sqrt(2 dt) (D(r_m) - D(r)) B^{-T} xi with that difference evaluated from
+ * the positions in FP32.  Errors: BD_ERR_ARG, BD_ERR_STATE, BD_ERR_CUDA. */
+int bd_midpoint(bd_ctx* ctx, const double* xi_dev, double* rmid_dev, double* y_dev, void* stream);
 
 /* Pathwise gradient of an objective J(r_final) with respect to the
  * Weissenberg number and h*, at fixed noise (the paper has no derivatives).
@@ -200,7 +221,8 @@ int bd_get_tensions(bd_ctx* ctx, double* T_dev, void* stream);
  * L' = L Phi(L^{-1} D' L^{-T}), of the Brownian and flow terms, and of the
  * tension solve by the implicit function theorem), which for two parameters
  * needs no checkpoints; ckpt_every is accepted and ignored.  The context is
- * left at the final state.  FP64 contexts with h* > 0 only (else BD_ERR_ARG).
+ * left at the final state.  FP64 contexts with h* > 0 and BD_SCHEME_EULER
+ * only (else BD_ERR_ARG).
  * Synchronises the stream; returns the most severe chain status. */
 int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noise_dev,
                int ckpt_every, const double* dJdr_final_dev, double grad_host[2], void* stream);
@@ -234,18 +256,22 @@ int bd_read_matrix(bd_ctx* ctx, int chain, int which, double* out_host);
  * synchronise the device) and therefore cannot create a bd_ctx.
  *
  * u = D(r) f for ONE chain of n_beads <= BD_STATIC_MAX_BEADS beads, with D the
- * RPY diffusion tensor of Sec. 3 Eqs. (7)-(9) evaluated on the fly from the
- * positions (h_star >= 0; a <= 0 means a = h_star; a < h_star is rejected).
- * r_dev, f_dev, u_dev: device FP64 [n_beads][3], owned by the caller.
+ * same RPY diffusion tensor the context assembles, evaluated on the fly from
+ * the positions (finite h_star >= 0; finite a, a <= 0 meaning a = h_star;
+ * a < h_star is rejected).
+ * r_dev, f_dev, u_dev: FP64 [n_beads][3] in memory of the CURRENT CUDA device
+ * (checked; other memory is rejected), owned by the caller.
  * It allocates nothing: its scratch is a fixed file-scope device array of
  * 786,432 bytes that every GPU loading the library holds until exit.  The
  * first call on each device looks up that array's device address (with the
  * device current) and caches it; make that first call before any stream
- * capture.  Every call shares the array and writes each slot before reading
- * it, so calls whose work overlaps on the GPU (other streams or host threads)
- * race and must be serialised by the caller.  Asynchronous on `stream`.
- * Errors: BD_ERR_ARG (NULL pointer, n_beads < 1 or > BD_STATIC_MAX_BEADS, bad
- * h_star/a), BD_ERR_CUDA. */
+ * capture, and do not call it again on a device after cudaDeviceReset of that
+ * device (the cached address is then stale).  Every call shares the array and
+ * writes each slot before reading it, so calls whose work overlaps on the GPU
+ * (other streams or host threads) race and must be serialised by the caller.
+ * Asynchronous on `stream`.
+ * Errors: BD_ERR_ARG (NULL pointer or memory of another device, n_beads < 1 or
+ * > BD_STATIC_MAX_BEADS, bad h_star/a), BD_ERR_CUDA. */
 #define BD_STATIC_MAX_BEADS 1024
 int bd_mobility_apply_static(const double* r_dev, int n_beads, double h_star, double a,
                              const double* f_dev, double* u_dev, void* stream);

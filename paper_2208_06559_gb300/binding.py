@@ -28,6 +28,7 @@ BD_ERR_STATE = -7
 FLOW_NONE, FLOW_SHEAR, FLOW_UNIAXIAL = 0, 1, 2
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
 RIGID, FRAENKEL = 0, 1
+SCHEME_MIDPOINT, SCHEME_EULER = 0, 1
 OBS_STRIDE = 12
 # column indices of the observables row (include/bd.h BD_OBS_*)
 OBS_REE_X, OBS_R2, OBS_RG2, OBS_STRETCH, OBS_MAXDEV, OBS_NEWTON = 0, 3, 4, 5, 6, 7
@@ -52,6 +53,7 @@ class Params(ctypes.Structure):
         ("max_newton", ctypes.c_int),
         ("refine", ctypes.c_int),
         ("k_spring", ctypes.c_double),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -75,6 +77,8 @@ EXPORTS = {
     "bd_mobility_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
     "bd_get_tensions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bd_midpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
     "bd_read_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_void_p]),
     "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -169,9 +173,12 @@ def mobility_apply_static(r, f, h_star: float = 0.25, a: float = 0.0, out=None, 
     if out is None:
         out = torch.empty_like(f)
     _f64(out, "mobility_apply_static: out", n, device=r.device.index)
-    _check(lib().bd_mobility_apply_static(_ptr(r), int(r.shape[0]), float(h_star), float(a),
-                                          _ptr(f), _ptr(out), _stream(stream)),
-           "bd_mobility_apply_static")
+    # the library works on the current device and its scratch array there
+    with torch.cuda.device(r.device):
+        st = stream if stream is not None else torch.cuda.current_stream(r.device)
+        _check(lib().bd_mobility_apply_static(_ptr(r), int(r.shape[0]), float(h_star), float(a),
+                                              _ptr(f), _ptr(out), _stream(st)),
+               "bd_mobility_apply_static")
     return out
 
 
@@ -185,7 +192,8 @@ class Context:
     def __init__(self, n_beads: Sequence[int], h_star: float = 0.25, dt: float = 1e-4,
                  flow: int = FLOW_NONE, Wi: float = 0.0, lam: float = 1.0, a: float = 0.0,
                  precision: int = FP64, tol: float = 1e-13, max_newton: int = 50,
-                 refine: int = 1, constraint: int = RIGID, k_spring: float = 1e4):
+                 refine: int = 1, constraint: int = RIGID, k_spring: float = 1e4,
+                 scheme: int = SCHEME_MIDPOINT):
         import torch
         L = lib()
         # the library's current device at creation (without CUDA, bd_create reports the error)
@@ -201,12 +209,13 @@ class Context:
         p.h_star, p.a, p.dt = float(h_star), float(a), float(dt)
         p.flow, p.Wi, p.lambda_ = int(flow), float(Wi), float(lam)
         p.precision, p.tol, p.max_newton, p.refine = int(precision), float(tol), int(max_newton), int(refine)
-        p.constraint, p.k_spring = int(constraint), float(k_spring)
+        p.constraint, p.k_spring, p.scheme = int(constraint), float(k_spring), int(scheme)
         h = ctypes.c_void_p()
         _check(L.bd_create(ctypes.byref(p), ctypes.byref(h)), "bd_create")
         self._h = h
         self.precision = int(precision)
         self.constraint = int(constraint)
+        self.scheme = int(scheme)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -353,6 +362,17 @@ class Context:
                "bd_mobility_apply")
         return u
 
+    def midpoint(self, xi, stream=None):
+        """Midpoint stage of the corrected rigid-rod step (after assemble and
+        factor): (r_m, y) with r_m = r + P y_B / 2 and y the step's Brownian
+        displacement sqrt(2 dt) D(r_m) B^{-T} xi."""
+        import torch
+        _f64(xi, "midpoint: xi", 3 * self.total_beads, self.device)
+        rm = torch.empty_like(xi)
+        y = torch.empty_like(xi)
+        _check(lib().bd_midpoint(self._h, _ptr(xi), _ptr(rm), _ptr(y), _stream(stream)), "bd_midpoint")
+        return rm, y
+
     def tensions(self, stream=None):
         import torch
         T = torch.zeros(max(self.total_rods, 1), dtype=torch.float64, device=f"cuda:{self.device}")
@@ -370,7 +390,8 @@ class Context:
 
 
 def simulate(Wi, h_star, n_beads, r0, noise, dt: float = 1e-4, flow: int = FLOW_UNIAXIAL,
-             lam: float = 1.0, tol: float = 1e-13, max_newton: int = 50, ckpt_every: int = 20):
+             lam: float = 1.0, tol: float = 1e-13, max_newton: int = 50, ckpt_every: int = 20,
+             scheme: int = SCHEME_EULER):
     """Final positions after noise.shape[0] FP64 steps from r0, differentiable
     with respect to the 0-dim float64 tensors Wi and h_star (a = h_star).
 
@@ -382,7 +403,7 @@ def simulate(Wi, h_star, n_beads, r0, noise, dt: float = 1e-4, flow: int = FLOW_
         @staticmethod
         def forward(ctx_, wi, hs):
             c = Context(n_beads, h_star=float(hs), dt=dt, flow=flow, Wi=float(wi), lam=lam, tol=tol,
-                        max_newton=max_newton)
+                        max_newton=max_newton, scheme=scheme)
             c.set_state(r0)
             c.step(noise)
             out = c.get_state()
@@ -398,7 +419,7 @@ def simulate(Wi, h_star, n_beads, r0, noise, dt: float = 1e-4, flow: int = FLOW_
         def backward(ctx_, grad_out):
             wi, hs = ctx_.saved_tensors
             c = Context(n_beads, h_star=float(hs), dt=dt, flow=flow, Wi=float(wi), lam=lam, tol=tol,
-                        max_newton=max_newton)
+                        max_newton=max_newton, scheme=scheme)
             gw, gh = c.adjoint(r0, noise, grad_out.contiguous(), ckpt_every)
             c.close()
             return (torch.tensor(gw, dtype=wi.dtype, device=wi.device),

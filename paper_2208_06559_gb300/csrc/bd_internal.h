@@ -100,8 +100,9 @@ enum MobMode : int { MOB_FULL_F32 = 0, MOB_FULL_DF = 1, MOB_INC_DF = 2, MOB_INC_
 cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, int max_np,
                             const double* f, float2* fsplit, double* scratch, double* u,
                             const int* state, cudaStream_t s);
-// Mixed path: K (FP32) and optionally G = C D C^T U (three planes [3][mp][mp]
-// per chain at 3 koff) from the positions, without D (k_matvec.cu).
+// Mixed path: K (FP32) and G = C D C^T U (three planes [3][mp][mp] per chain
+// at 3 koff) from the positions, without D (k_matvec.cu); either output may
+// be NULL.
 cudaError_t launch_form_k_pos(const double* r, float* K, float* G, const ChainDesc* cd, int n_chains,
                               int max_m, const double* u, double hstar, double a, cudaStream_t s);
 template <typename T>
@@ -140,7 +141,9 @@ cudaError_t launch_tension_products_g(const float* G, const ChainDesc* cd, int n
 cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const ChainDesc* cd,
                                      int n_chains, Phys ph, double* rhs, int* state, int* status,
                                      const int* iters, int* mode, cudaStream_t s);
-cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const float* M, const double* rstar,
+// rpos: the positions whose mobility moves bead 0 ((D F)_0 is evaluated from
+// them in FP64): the start of the step, or the midpoint of the corrected step.
+cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const double* rpos, const double* rstar,
                               const double* w, const double* F, double* r, const int* state, int* status,
                               StepArgs* args, cudaStream_t s);
 cudaError_t gmode_configure();
@@ -173,7 +176,7 @@ cudaError_t launch_fraenkel_update(double* r, const double* y, const double* u, 
 cudaError_t launch_step_done(StepArgs* args, cudaStream_t s);
 // Kernels of the rod-coupling-matrix chain (K formation and factorisation),
 // for per-node priorities in the captured step graph.
-const void* form_k_pos_kernel();
+bool is_kchain_form_kernel(const void* f);  // K (with or without G) from the positions
 bool is_k64_kernel(const void* f);
 const void* rod_dirs_kernel();
 cudaError_t refine_configure();
@@ -182,11 +185,29 @@ cudaError_t refine_configure();
 // y = s/2 (B xi + D B^{-T} xi); with refine == 0, y = s B xi.
 // The triangular solve of the refinement runs on `s2` (forked from and joined
 // back into `s` with events ev[0], ev[1]) concurrently with the product.
+// need_z: leave z = B^{-T} xi (unscaled) in `z` also when refine == 0.
 cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
                                 double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
-                                cudaEvent_t* ev);
+                                cudaEvent_t* ev, bool need_z = false);
+
+// Midpoint corrector of the rigid-rod step (k_midpoint.cu).
+// r_m = r + P y / 2 (P: orthogonal projection onto the tangent space of the
+// rod constraints at r) into rmid, the unit rod directions of r_m into umid;
+// y = yscale * y (or yscale * the step's noise when args != NULL).
+cudaError_t launch_tangent_midpoint(const double* r, const double* y, const StepArgs* args, double yscale,
+                                    const ChainDesc* cd, int n_chains, const int* status, double* rmid,
+                                    double* umid, cudaStream_t s);
+// z = scale L^{-T} xi for the FP64 factor (xi from x, or the step's noise when args != NULL).
+cudaError_t launch_trsv_t_f64(const double* M, const double* Winv, const ChainDesc* cd, int n_chains,
+                              int max_n, const double* x, const StepArgs* args, double scale, double* z,
+                              cudaStream_t s);
+// y += scale (D(rmid) - D(r)) z, from the positions in FP32 (mixed path).
+cudaError_t launch_mob_delta_f32(const double* r, const double* rmid, const double* z, const ChainDesc* cd,
+                                 int n_chains, int max_N, const int* status, double hstar, double a,
+                                 double scale, double* y, cudaStream_t s);
+cudaError_t midpoint_configure();
 
 // Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
 bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, const ChainDesc* h_cd,

@@ -87,6 +87,11 @@ struct bd_ctx {
   int while_cap = 1;     // WHILE-node iterations allowed per step
   cudaEvent_t* prof = nullptr;  // bd_profile_step: stage-boundary events
   bool fraenkel = false;        // BD_FRAENKEL: semi-implicit spring update instead of the tension solve
+  bool midpoint = false;        // rigid rods, BD_SCHEME_MIDPOINT: mobility and rod directions at r_m
+  double* rmid = nullptr;       // midpoint positions r_m, [sum N][3]
+  double* umid = nullptr;       // unit rod directions of r_m, [sum (N-1)][3]
+  double* rK = nullptr;         // mixed midpoint path: positions at which K is formed, [sum N][3]
+  void* M2 = nullptr;           // FP64 midpoint path: D(r_m), full symmetric, layout of M
   std::mutex mu;
 };
 
@@ -165,12 +170,13 @@ int enqueue_brownian(bd_ctx* c, const double* x, const StepArgs* args, double* y
   return BD_OK;
 }
 
-int enqueue_symv(bd_ctx* c, const double* f, double* u, const int* state, cudaStream_t s) {
+// u = D f with the matrix `Mat` (the context's M, or the midpoint matrix M2).
+int enqueue_symv(bd_ctx* c, const void* Mat, const double* f, double* u, const int* state, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_symv_f32((const float*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->fsplit, c->scratch, u,
+    CK(launch_symv_f32((const float*)Mat, c->d_cd, c->n_chains, c->max_np, f, c->fsplit, c->scratch, u,
                        state, s));
   else
-    CK(launch_symv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
+    CK(launch_symv<double>((const double*)Mat, c->d_cd, c->n_chains, c->max_np, f, c->scratch, u,
                            state, s));
   return BD_OK;
 }
@@ -180,10 +186,86 @@ void prof_mark(bd_ctx* c, int i, cudaStream_t s) {
   if (c->prof) cudaEventRecord(c->prof[i], s);
 }
 
+// Midpoint step, FP64 path: D and its factor at r, y = s L xi and
+// z = s L^{-T} xi (in F, free until the predictor), r_m and its rod
+// directions, D(r_m) assembled into M2; then the K chain (K of D(r_m) and
+// the directions of r_m, its factor) beside the product y = D(r_m) z.
+int enqueue_pre_newton_mid_fp64(bd_ctx* c, cudaStream_t s) {
+  int rc;
+  cudaStream_t sk = c->aux[0];
+  if ((rc = enqueue_assemble(c, s))) return rc;
+  prof_mark(c, 1, s);
+  if ((rc = enqueue_factor(c, s))) return rc;
+  prof_mark(c, 2, s);
+  CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, nullptr, c->args, c->ph.sq2dt,
+                         c->y, s));
+  CK(launch_trsv_t_f64((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, c->max_n, nullptr,
+                       c->args, c->ph.sq2dt, c->F, s));
+  CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+  CK(launch_assemble<double>(c->rmid, (double*)c->M2, c->d_cd, c->n_chains, c->max_N, c->max_np, c->ph.hstar,
+                             c->ph.a, nullptr, s));
+  CK(cudaEventRecord(c->aev[0], s));
+  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  CK(launch_form_k<double>((const double*)c->M2, (double*)c->K, c->d_cd, c->n_chains, c->max_m, c->umid, sk));
+  CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / kSimtTile,
+                              true, c->status, sk));
+  prof_mark(c, 7, sk);
+  CK(cudaEventRecord(c->aev[1], sk));
+  if ((rc = enqueue_symv(c, c->M2, c->F, c->y, nullptr, s))) return rc;
+  prof_mark(c, 3, s);
+  CK(cudaStreamWaitEvent(s, c->aev[1], 0));
+  CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->umid, c->T, c->F,
+                      c->state, c->status, c->iters, nullptr, s));
+  prof_mark(c, 4, s);
+  return BD_OK;
+}
+
+// Midpoint step, mixed path.  The K chain preconditions the tension
+// iteration and runs beside the factorisation as in the Euler step (the
+// root of the iteration does not depend on it): K is formed at an estimate
+// of the midpoint that needs no factor, r + P (s xi) / 2 (the Brownian
+// displacement without HI), with that estimate's rod directions, then
+// factored with its super-block inverses.  The main chain: D and its
+// tensor-core factor at r, the refined y and z = Lt^{-T} xi (in F), r_m and
+// its rod directions, y += s (D(r_m) - D(r)) z from the positions, G of r_m,
+// the predictor.
+int enqueue_pre_newton_mid_mixed(bd_ctx* c, cudaStream_t s) {
+  int rc;
+  cudaStream_t sk = c->aux[0];
+  CK(cudaEventRecord(c->aev[0], s));
+  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  if ((rc = enqueue_assemble(c, s))) return rc;
+  prof_mark(c, 1, s);
+  CK(launch_tangent_midpoint(c->r, nullptr, c->args, c->ph.sq2dt, c->d_cd, c->n_chains, c->status, c->rK,
+                             c->uhat, sk));
+  CK(launch_form_k_pos(c->rK, (float*)c->K, nullptr, c->d_cd, c->n_chains, c->max_m, c->uhat, c->ph.hstar,
+                       c->ph.a, sk));
+  CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64, c->status, sk));
+  CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
+  prof_mark(c, 7, sk);
+  CK(cudaEventRecord(c->aev[1], sk));
+  if ((rc = enqueue_factor(c, s))) return rc;
+  prof_mark(c, 2, s);
+  CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, nullptr, c->args,
+                         c->ph.sq2dt, c->p.refine != 0, c->y, c->rT, c->F, c->u, c->scratch, c->fsplit, s,
+                         c->aux[1], c->aev + 2, true));
+  CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+  CK(launch_mob_delta_f32(c->r, c->rmid, c->F, c->d_cd, c->n_chains, c->max_N, c->status, c->ph.hstar, c->ph.a,
+                          c->ph.sq2dt, c->y, s));
+  CK(launch_form_k_pos(c->rmid, nullptr, c->G, c->d_cd, c->n_chains, c->max_m, c->umid, c->ph.hstar, c->ph.a,
+                       s));
+  prof_mark(c, 3, s);
+  CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->umid, c->T, c->F,
+                      c->state, c->status, c->iters, c->accurate, s));
+  prof_mark(c, 4, s);
+  return BD_OK;
+}
+
 // Before the tension solve.  The K chain (rod directions, K, its factor)
 // needs only the old positions and the upper-triangle D, so it runs on its
 // own stream while D is factored and the Brownian displacement is formed.
 int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
+  if (c->midpoint) return c->mixed ? enqueue_pre_newton_mid_mixed(c, s) : enqueue_pre_newton_mid_fp64(c, s);
   int rc;
   cudaStream_t sk = c->aux[0];
   if (c->mixed) {
@@ -233,22 +315,23 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
 // first iteration, whose solve waits for the end of the K chain (K's factor
 // and its super-block inverses) -- the product and residual run beside it.
 int enqueue_newton_iter(bd_ctx* c, cudaStream_t s, bool first = false) {
+  const double* udir = c->midpoint ? c->umid : c->uhat;
   if (c->mixed) {
     CK(launch_tension_products_g(c->G, c->d_cd, c->n_chains, c->max_mp, c->T, c->dT, c->u, c->state,
                                  c->accurate, s));
     CK(launch_newton_residual_g(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rhs, c->state, c->status,
                                 c->iters, c->accurate, s));
     if (first) CK(cudaStreamWaitEvent(s, c->aev[1], 0));
-    CK(launch_newton_solve_sb((const float*)c->K, c->Vsb, c->d_cd, c->n_chains, c->ph, c->uhat, c->rhs, c->T,
+    CK(launch_newton_solve_sb((const float*)c->K, c->Vsb, c->d_cd, c->n_chains, c->ph, udir, c->rhs, c->T,
                               c->F, c->state, c->iters, c->dT, s));
     return BD_OK;
   }
   int rc;
-  if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+  if ((rc = enqueue_symv(c, c->midpoint ? c->M2 : c->M, c->F, c->u, c->state, s))) return rc;
   CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
                             c->status, c->iters, s));
   CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains, c->ph,
-                                 c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
+                                 udir, c->rhs, c->T, c->F, c->state, c->iters, s));
   return BD_OK;
 }
 
@@ -256,8 +339,8 @@ int enqueue_newton_iter(bd_ctx* c, cudaStream_t s, bool first = false) {
 // the rods), step index advanced.
 int enqueue_finalize(bd_ctx* c, cudaStream_t s) {
   if (c->mixed)
-    CK(launch_finalize_g(c->d_cd, c->n_chains, c->ph, (const float*)c->M, c->rstar, c->u, c->F, c->r, c->state,
-                         c->status, c->args, s));
+    CK(launch_finalize_g(c->d_cd, c->n_chains, c->ph, c->midpoint ? c->rmid : c->r, c->rstar, c->u, c->F, c->r,
+                         c->state, c->status, c->args, s));
   else
     CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status, c->args,
                        s));
@@ -300,7 +383,7 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
     const bool kchain = c->mixed && (kp.func == rod_dirs_kernel() ||
-                                     is_k64_kernel(kp.func) || kp.func == form_k_pos_kernel() ||
+                                     is_k64_kernel(kp.func) || is_kchain_form_kernel(kp.func) ||
                                      is_sb_inverse_kernel(kp.func));
     cudaLaunchAttributeValue v;
     memset(&v, 0, sizeof(v));
@@ -324,7 +407,7 @@ int enqueue_step_fraenkel(bd_ctx* c, cudaStream_t s) {
   if ((rc = enqueue_brownian(c, nullptr, c->args, c->y, s))) return rc;
   prof_mark(c, 3, s);
   CK(launch_fraenkel_forces(c->r, c->d_cd, c->n_chains, c->max_N, c->ph.kspring, c->F, s));
-  if ((rc = enqueue_symv(c, c->F, c->u, nullptr, s))) return rc;
+  if ((rc = enqueue_symv(c, c->M, c->F, c->u, nullptr, s))) return rc;
   prof_mark(c, 4, s);
   CK(launch_fraenkel_update(c->r, c->y, c->u, c->d_cd, c->n_chains, c->ph, c->T, c->status, c->iters, s));
   prof_mark(c, 5, s);
@@ -559,7 +642,7 @@ void bd_destroy(bd_ctx* c) {
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
                   c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
-                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot};
+                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2, c->rK};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
@@ -586,9 +669,11 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   const double a = p->a > 0.0 ? p->a : p->h_star;
   if (p->h_star > 0.0 && a < p->h_star) return BD_ERR_ARG;  // D may not be positive definite
   if (p->flow < BD_FLOW_NONE || p->flow > BD_FLOW_UNIAXIAL) return BD_ERR_ARG;
-  if (p->precision < BD_FP64 || p->precision > BD_MIXED_BF16) return BD_ERR_ARG;
+  // BD_MIXED_BF16 names a factorisation with BF16 operands, which is not built
+  if (p->precision != BD_FP64 && p->precision != BD_MIXED_TF32) return BD_ERR_ARG;
   if (p->constraint != BD_RIGID && p->constraint != BD_FRAENKEL) return BD_ERR_ARG;
   if (p->constraint == BD_FRAENKEL && !(p->k_spring > 0.0 && p->k_spring < 1e300)) return BD_ERR_ARG;
+  if (p->scheme != BD_SCHEME_MIDPOINT && p->scheme != BD_SCHEME_EULER) return BD_ERR_ARG;
   // limits of the per-chain kernels: the tension solve holds N - 1 <= 4096
   // unknowns in shared memory; the refinement's triangular solve owns up to
   // 12 columns per thread of a 1024-thread block (3N <= 12288 after padding)
@@ -625,6 +710,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   ph.n_chains = c->n_chains;
   ph.kspring = p->constraint == BD_FRAENKEL ? p->k_spring : 0.0;
   c->fraenkel = p->constraint == BD_FRAENKEL;
+  c->midpoint = !c->fraenkel && p->scheme == BD_SCHEME_MIDPOINT;
   if (const char* e = getenv("BD_STEP_DIRECT")) {
     const int v = atoi(e);
     c->direct_iters = v > 0 ? (v == 1 ? ph.max_newton + 2 : v) : 0;
@@ -709,6 +795,9 @@ int bd_create(const bd_params* p, bd_ctx** out) {
          alloc((void**)&c->Vsb, (size_t)kwrow * 256 * sizeof(float)) &&
          alloc((void**)&c->M16, c->M_elems * sizeof(__half)) &&
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (2 * c->n_chains + 1));
+  if (ok && c->midpoint)
+    ok = alloc((void**)&c->rmid, b3) && alloc((void**)&c->umid, 3 * rr) &&
+         (c->mixed ? alloc((void**)&c->rK, b3) : alloc(&c->M2, c->M_elems * sizeof(double)));
   if (!ok) {
     bd_destroy(c);
     return BD_ERR_OOM;
@@ -754,7 +843,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
       assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
       k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess ||
-      solve_sb_configure() != cudaSuccess)
+      solve_sb_configure() != cudaSuccess || midpoint_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -775,6 +864,9 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   } else {
     e1 = launch_fill_identity_border<double>((double*)c->M, c->d_cd, c->n_chains, c->max_np, false, s);
     e2 = launch_fill_identity_border<double>((double*)c->K, c->d_cd, c->n_chains, c->max_mp, true, s);
+    if (c->M2 && e1 == cudaSuccess) e1 = cudaMemsetAsync(c->M2, 0, c->M_elems * sizeof(double), s);
+    if (c->M2 && e1 == cudaSuccess)
+      e1 = launch_fill_identity_border<double>((double*)c->M2, c->d_cd, c->n_chains, c->max_np, false, s);
   }
   if (e1 != cudaSuccess || e2 != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
     return fail(BD_ERR_CUDA);
@@ -942,7 +1034,7 @@ int bd_brownian(bd_ctx* c, const double* xi_dev, double* y_dev, void* stream) {
 int bd_mobility_apply(bd_ctx* c, const double* f_dev, double* u_dev, void* stream) {
   if (!c || !f_dev || !u_dev) return BD_ERR_ARG;
   DeviceGuard g(c->device);
-  return enqueue_symv(c, f_dev, u_dev, nullptr, (cudaStream_t)stream);
+  return enqueue_symv(c, c->M, f_dev, u_dev, nullptr, (cudaStream_t)stream);
 }
 
 int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
@@ -954,11 +1046,40 @@ int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
   return BD_OK;
 }
 
+int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev, void* stream) {
+  if (!c || !xi_dev || !rmid_dev || !y_dev || !c->midpoint) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->mixed) {
+    CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, xi_dev, nullptr,
+                           c->ph.sq2dt, c->p.refine != 0, c->y, c->rT, c->F, c->u, c->scratch, c->fsplit, s,
+                           c->aux[1], c->aev + 2, true));
+    CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+    CK(launch_mob_delta_f32(c->r, c->rmid, c->F, c->d_cd, c->n_chains, c->max_N, c->status, c->ph.hstar,
+                            c->ph.a, c->ph.sq2dt, c->y, s));
+  } else {
+    CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, xi_dev, nullptr, c->ph.sq2dt,
+                           c->y, s));
+    CK(launch_trsv_t_f64((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, c->max_n, xi_dev,
+                         nullptr, c->ph.sq2dt, c->F, s));
+    CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+    CK(launch_assemble<double>(c->rmid, (double*)c->M2, c->d_cd, c->n_chains, c->max_N, c->max_np,
+                               c->ph.hstar, c->ph.a, nullptr, s));
+    int rc = enqueue_symv(c, c->M2, c->F, c->y, nullptr, s);
+    if (rc) return rc;
+  }
+  const size_t b3 = (size_t)c->total_beads * 3 * sizeof(double);
+  CK(cudaMemcpyAsync(rmid_dev, c->rmid, b3, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(y_dev, c->y, b3, cudaMemcpyDeviceToDevice, s));
+  return BD_OK;
+}
+
 int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
                const double* dJdr_final_dev, double grad_host[2], void* stream) {
   (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
   if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
-  if (c->mixed || c->fraenkel || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
+  if (c->mixed || c->fraenkel || c->midpoint || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1013,7 +1134,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
     CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
                         c->F, c->state, c->status, c->iters, nullptr, s));
     for (int it = 0; it < iters_max; ++it) {
-      if ((rc = enqueue_symv(c, c->F, c->u, c->state, s))) return rc;
+      if ((rc = enqueue_symv(c, c->M, c->F, c->u, c->state, s))) return rc;
       CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
                                 c->status, c->iters, s));
       CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
@@ -1036,12 +1157,12 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
                              c->ph.sq2dt, c->ydot, s));
       CK(launch_tangent_predictor(c->r, rd, c->ydot, c->uhat, c->T, c->d_cd, c->n_chains, c->max_N, c->ph,
                                   c->kdot + 9 * p, c->rsdot, c->Gt, s));
-      if ((rc = enqueue_symv(c, c->Gt, c->DG, nullptr, s))) return rc;
+      if ((rc = enqueue_symv(c, c->M, c->Gt, c->DG, nullptr, s))) return rc;
       CK(launch_tangent_base(c->d_cd, c->n_chains, c->max_n, c->ph, c->rsdot, c->DdF, c->DG, c->abase, s));
       CK(launch_tangent_init(c->d_cd, c->n_chains, c->max_n, c->status, c->state, c->iters, c->Tdot,
                              c->Fdot, s));
       for (int it = 0; it < iters_max; ++it) {
-        if ((rc = enqueue_symv(c, c->Fdot, c->u, c->state, s))) return rc;
+        if ((rc = enqueue_symv(c, c->M, c->Fdot, c->u, c->state, s))) return rc;
         CK(launch_tangent_residual(c->abase, c->u, c->rT, c->d_cd, c->n_chains, c->ph, 1e-12, c->rscale,
                                    c->zt, c->rhs, c->state, c->status, c->iters, s));
         CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,

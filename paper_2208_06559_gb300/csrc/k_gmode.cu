@@ -19,6 +19,7 @@
 //   k_finalize_g     : positions of converged chains from the rods.
 #include "bd_internal.h"
 #include "block_dev.h"
+#include "rpy_dev.h"
 #include "pdl.h"
 
 namespace bd {
@@ -206,15 +207,15 @@ __global__ void __launch_bounds__(256) k_newton_residual_g(const double* __restr
 }
 
 // One CTA (1024 threads) per chain, converged chains only: bead 0 moves by
-// dt (D F)_0 (D_0j, Eqs. (7)-(9), read from rows 0-2 of the stored FP32
-// mobility matrix, whose upper triangle still holds D; D_00 = I) and the
-// rods Q_k = Q*_k - dt w_k are summed from it.  Failed chains keep their
+// dt (D F)_0 (D_0j, Eqs. (7)-(9), evaluated in FP64 from the positions whose
+// mobility the step uses; D_00 = I) and the rods Q_k = Q*_k - dt w_k are
+// summed from it.  Failed chains keep their
 // positions; the step index advances as in k_finalize.
 constexpr int kFinThreads = 1024;
 constexpr int kFinPer = 4;  // beads per thread (N <= 4096)
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __restrict__ cd, Phys ph,
-                                                            const float* __restrict__ M,
+                                                            const double* __restrict__ rpos,
                                                             const double* __restrict__ rstar,
                                                             const double* __restrict__ w,
                                                             const double* __restrict__ F,
@@ -236,10 +237,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __r
   double* rc = r + 3 * d.boff;
   const double* rs = rstar + 3 * d.boff;
   const double* Fc = F + 3 * d.boff;
-  // (D F)_0 from row block 0 of D
+  // (D F)_0 with the RPY blocks D_0j (Sec. 3 Eqs. (8)-(9)) of rpos, in FP64
   double df[3] = {0.0, 0.0, 0.0};
-  const float* M0 = M + d.moff;
-  const long long np = d.np;
+  const double* rp = rpos + 3 * d.boff;
   for (int j = t; j < N; j += kFinThreads) {
     const double f0 = Fc[3 * j], f1 = Fc[3 * j + 1], f2 = Fc[3 * j + 2];
     if (j == 0) {
@@ -247,11 +247,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __r
       df[1] += f1;
       df[2] += f2;
     } else {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float* row = M0 + q * np + 3 * j;
-        df[q] += (double)row[0] * f0 + (double)row[1] * f1 + (double)row[2] * f2;
-      }
+      const double R0 = rp[0] - rp[3 * j], R1 = rp[1] - rp[3 * j + 1], R2 = rp[2] - rp[3 * j + 2];
+      double cI, cRR;
+      rpy_coeffs<double>(R0 * R0 + R1 * R1 + R2 * R2, ph.hstar, ph.a, cI, cRR);
+      const double rf = cRR * (R0 * f0 + R1 * f1 + R2 * f2);
+      df[0] += cI * f0 + rf * R0;
+      df[1] += cI * f1 + rf * R1;
+      df[2] += cI * f2 + rf * R2;
     }
   }
   block_sum3(df, red);
@@ -295,10 +297,10 @@ cudaError_t launch_newton_residual_g(const double* rstar, const double* w, const
                     iters, mode);
 }
 
-cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const float* M, const double* rstar,
+cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const double* rpos, const double* rstar,
                               const double* w, const double* F, double* r, const int* state, int* status,
                               StepArgs* args, cudaStream_t s) {
-  k_finalize_g<<<n_chains, kFinThreads, 0, s>>>(cd, ph, M, rstar, w, F, r, state, status, args);
+  k_finalize_g<<<n_chains, kFinThreads, 0, s>>>(cd, ph, rpos, rstar, w, F, r, state, status, args);
   return cudaGetLastError();
 }
 

@@ -271,10 +271,16 @@ __global__ void __launch_bounds__(256) k_form_k(const T* __restrict__ M, T* __re
 // ~1e-7 relative change of the model, far below the TF32 factor's).
 constexpr int KB = KR + 1;  // beads per tile side
 
+// WHAT selects the outputs (bit 0: K, bit 1: G); the variants are separate
+// kernels so that the step graph can give the K chain's launches their own
+// priority.
+template <int WHAT>
 __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r, float* __restrict__ K,
                                                     float* __restrict__ G,
                                                     const ChainDesc* __restrict__ cd,
                                                     const double* __restrict__ uhat, float hstar, float arad) {
+  if (!(WHAT & 1)) K = nullptr;
+  if (!(WHAT & 2)) G = nullptr;
   __shared__ float Ds[6][KB][KB];  // xx, xy, xz, yy, yz, zz of D_xy
   __shared__ float ph[2][KB][3], pl[2][KB][3];  // split positions: [0] k side, [1] l side
   __shared__ float uk[KR][3], ul[KR][3];
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
     const float bv[3] = {B[0] * v0 + B[1] * v1 + B[2] * v2, B[1] * v0 + B[3] * v1 + B[4] * v2,
                          B[2] * v0 + B[4] * v1 + B[5] * v2};  // B u_l
     if (valid) {
-      K[d.koff + (long long)k * mp + l] = u0 * bv[0] + u1 * bv[1] + u2 * bv[2];
+      if (K) K[d.koff + (long long)k * mp + l] = u0 * bv[0] + u1 * bv[1] + u2 * bv[2];
       if (Gc) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) Gc[q * mp * mp + (long long)k * mp + l] = bv[q];
@@ -377,7 +383,13 @@ __global__ void __launch_bounds__(256) k_form_k_pos(const double* __restrict__ r
 cudaError_t launch_form_k_pos(const double* r, float* K, float* G, const ChainDesc* cd, int n_chains,
                               int max_m, const double* u, double hstar, double a, cudaStream_t s) {
   const int TK = ceil_div(max_m, KR);
-  k_form_k_pos<<<dim3(TK * (TK + 1) / 2, n_chains), 256, 0, s>>>(r, K, G, cd, u, (float)hstar, (float)a);
+  const dim3 grid(TK * (TK + 1) / 2, n_chains);
+  if (K && G)
+    k_form_k_pos<3><<<grid, 256, 0, s>>>(r, K, G, cd, u, (float)hstar, (float)a);
+  else if (K)
+    k_form_k_pos<1><<<grid, 256, 0, s>>>(r, K, G, cd, u, (float)hstar, (float)a);
+  else if (G)
+    k_form_k_pos<2><<<grid, 256, 0, s>>>(r, K, G, cd, u, (float)hstar, (float)a);
   return cudaGetLastError();
 }
 
@@ -624,7 +636,9 @@ cudaError_t launch_symv_f32(const float* M, const ChainDesc* cd, int n_chains, i
   return cudaGetLastError();
 }
 
-const void* form_k_pos_kernel() { return (const void*)k_form_k_pos; }
+bool is_kchain_form_kernel(const void* f) {
+  return f == (const void*)k_form_k_pos<3> || f == (const void*)k_form_k_pos<1>;
+}
 
 cudaError_t matvec_configure() {
   return cudaFuncSetAttribute(k_form_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,

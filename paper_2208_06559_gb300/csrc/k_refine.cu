@@ -276,9 +276,9 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
                                 int max_np, const double* x, const StepArgs* args, double scale,
                                 bool refine, double* y, double* y1, double* z, double* w,
                                 double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
-                                cudaEvent_t* ev) {
+                                cudaEvent_t* ev, bool need_z) {
   k_split<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, x, args, scratch);
-  if (!refine) {
+  if (!refine && !need_z) {
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
     return cudaGetLastError();
   }
@@ -287,10 +287,14 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
   if (e != cudaSuccess) return e;
   k_trsv_t_f32c<<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
-  k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
+  if (refine)
+    k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
+  else
+    k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
   e = cudaEventRecord(ev[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e != cudaSuccess) return e;
+  if (!refine) return cudaGetLastError();
   e = launch_symv_f32(M, cd, n_chains, max_np, z, fsplit, scratch, w, nullptr, s);
   if (e != cudaSuccess) return e;
   k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);

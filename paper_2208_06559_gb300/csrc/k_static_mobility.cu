@@ -11,8 +11,15 @@
 //
 // The kernels are the same deterministic two-phase SYMV as the context's
 // mobility product (tile partial sums, then a fixed-order reduction), with the
-// RPY blocks (Sec. 3 Eqs. (7)-(9)) evaluated on the fly from the positions
-// instead of read from an assembled matrix.
+// RPY blocks evaluated on the fly from the positions (the coefficients of
+// rpy_dev.h, shared with the assembly) instead of read from a matrix.
+//
+// Device.  The call works on the current CUDA device: its pointers must be
+// memory of that device (checked), and the scratch array used is that
+// device's copy.  The array's device address is looked up the first time the
+// call runs on a device and then cached; a cudaDeviceReset of that device
+// invalidates the cached address, so do not call this after resetting a
+// device it has already run on.
 //
 // Scratch: g_static_scratch holds kStaticTiles x kStaticTiles x 32 x 3 FP64
 // partial sums (786,432 bytes) for chains of at most BD_STATIC_MAX_BEADS =
@@ -23,9 +30,11 @@
 // threads) race on it and give wrong results.  Serialise them.
 #include <math.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "bd_internal.h"
+#include "rpy_dev.h"
 
 namespace {
 
@@ -45,21 +54,8 @@ double* g_scratch_ptr[kMaxDevices] = {nullptr};
 __device__ __forceinline__ void rpy_block64(const double* ri, const double* rj, double hstar,
                                             double a, double blk[9]) {
   const double R[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
-  const double R2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-  const double Rn = sqrt(R2);
   double cI, cRR;
-  if (hstar == 0.0) {
-    cI = 0.0;
-    cRR = 0.0;
-  } else if (Rn >= 2.0 * a) {
-    const double pref = 0.75 * hstar / Rn, a2R2 = a * a / R2;
-    cI = pref * (1.0 + 2.0 / 3.0 * a2R2);
-    cRR = pref * (1.0 - 2.0 * a2R2) / R2;
-  } else {
-    const double pref = 0.375 * hstar / a;
-    cI = pref * (8.0 / 3.0 - 0.75 * Rn / a);
-    cRR = (Rn > 0.0) ? pref * (0.25 / a) / Rn : 0.0;
-  }
+  bd::rpy_coeffs<double>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, a, cI, cRR);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -160,15 +156,29 @@ int static_scratch(double** out) {
   return BD_OK;
 }
 
+// True when p is memory of the current device (device or managed memory).
+bool on_current_device(const void* p) {
+  int dev = 0;
+  cudaPointerAttributes at;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" int bd_mobility_apply_static(const double* r_dev, int n_beads, double h_star,
                                         double a, const double* f_dev, double* u_dev,
                                         void* stream) {
-  if (!r_dev || !f_dev || !u_dev || n_beads < 1 || !(h_star >= 0.0)) return BD_ERR_ARG;
+  if (!r_dev || !f_dev || !u_dev || n_beads < 1) return BD_ERR_ARG;
+  if (!std::isfinite(h_star) || !(h_star >= 0.0) || !std::isfinite(a)) return BD_ERR_ARG;
   if (n_beads > kStaticMaxBeads) return BD_ERR_ARG;  // beyond the fixed scratch
   const double aa = a > 0.0 ? a : h_star;
   if (h_star > 0.0 && aa < h_star) return BD_ERR_ARG;
+  if (!on_current_device(r_dev) || !on_current_device(f_dev) || !on_current_device(u_dev)) return BD_ERR_ARG;
   double* P = nullptr;
   const int rc = static_scratch(&P);
   if (rc != BD_OK) return rc;

@@ -71,7 +71,7 @@ class Workload:
     flow: int               # 0 none, 1 shear, 2 uniaxial
     Wi: float
     n_steps: int
-    precision: int          # 0 fp64, 1 mixed tf32, 2 mixed bf16
+    precision: int          # 0 fp64, 1 mixed (TF32 panel solves, FP16-operand updates)
     seed: int
     uneven: tuple = ()      # (lo, hi) for drawn lengths
     constraint: int = 0     # 0 rigid rods (tension solve), 1 Fraenkel springs

@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--Wi", type=float, default=100.0)
     ap.add_argument("--dt", type=float, default=1e-4)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--scheme", default="midpoint", choices=["midpoint", "euler"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--once", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated bead counts: time one step per N")
@@ -45,7 +46,8 @@ def main():
     prec = bd.FP64 if a.precision == "fp64" else bd.MIXED_TF32
     Nc = np.full(a.chains, a.beads, np.int32)
     r0 = torch.from_numpy(inputs.random_walk(Nc, a.seed)).cuda()
-    ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec)
+    ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec,
+                     scheme=bd.SCHEME_MIDPOINT if a.scheme == "midpoint" else bd.SCHEME_EULER)
     ctx.set_state(r0)
     xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 3, int(Nc.sum()), a.seed + 1)).cuda()
     if a.timeline:

@@ -47,7 +47,7 @@ def test_strerror_and_defaults(lib):
     lib.bd_params_default(ctypes.byref(p))
     assert p.n_chains == 1 and p.h_star == 0.25 and p.dt == 1e-4 and p.tol == 1e-13
     assert p.max_newton == 50 and p.precision == 0
-    assert p.constraint == 0 and p.k_spring == 1e4
+    assert p.constraint == 0 and p.k_spring == 1e4 and p.scheme == 0
 
 
 @pytest.mark.parametrize("mutate", [
@@ -57,6 +57,8 @@ def test_strerror_and_defaults(lib):
     lambda p, nb: (setattr(p, "h_star", 0.5), setattr(p, "a", 0.25)),  # a < h*: not PD
     lambda p, nb: setattr(p, "flow", 7),
     lambda p, nb: setattr(p, "precision", 9),
+    lambda p, nb: setattr(p, "precision", 2),   # BF16 operands: no such factorisation is built
+    lambda p, nb: setattr(p, "scheme", 2),
     lambda p, nb: nb.__setitem__(0, 1),   # a chain needs >= 2 beads
     lambda p, nb: nb.__setitem__(1, 4097),  # past the per-chain kernel limit of 4096 beads
     lambda p, nb: setattr(p, "dt", float("nan")),

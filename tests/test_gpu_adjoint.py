@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 
 NC = np.array([12, 20, 7], np.int32)
 STEPS, DT, WI, HS, FD = 15, 1e-3, 5.0, 0.25, 1e-5
+SCHEME = 1  # the Euler rigid-rod step (the tangents follow that step map)
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +39,7 @@ def stretch_and_grad(r, Nc):
 
 
 def gpu_run(bd, r0, noise, Wi, hs):
-    ctx = bd.Context(NC, h_star=hs, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=Wi)
+    ctx = bd.Context(NC, h_star=hs, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=Wi, scheme=SCHEME)
     ctx.set_state(torch.from_numpy(r0).cuda())
     ctx.step(torch.from_numpy(noise).cuda())
     r = ctx.get_state().cpu().numpy()
@@ -49,7 +50,7 @@ def gpu_run(bd, r0, noise, Wi, hs):
 
 
 def oracle_run(r0, noise, Wi, hs):
-    p = orc.make_params(hstar=hs, dt=DT, flow=orc.FLOW_UNIAXIAL, Wi=Wi)
+    p = orc.make_params(hstar=hs, dt=DT, flow=orc.FLOW_UNIAXIAL, Wi=Wi, scheme=SCHEME)
     r, _, st, _, _ = orc.run(p, NC, r0, noise)
     assert (st == 0).all()
     return r
@@ -58,7 +59,7 @@ def oracle_run(r0, noise, Wi, hs):
 def test_adjoint_matches_finite_differences(bd):
     r0 = inputs.random_walk(NC, 501)
     noise = inputs.gaussian_noise(STEPS, int(NC.sum()), 502)
-    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI)
+    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=SCHEME)
     r_fin = gpu_run(bd, r0, noise, WI, HS)
     J0, dJdr = stretch_and_grad(r_fin, NC)
     gw, gh = ctx.adjoint(torch.from_numpy(r0).cuda(), torch.from_numpy(noise).cuda(),
@@ -80,11 +81,11 @@ def test_autograd_function(bd):
     noise = torch.from_numpy(inputs.gaussian_noise(8, int(NC.sum()), 504)).cuda()
     Wi = torch.tensor(WI, dtype=torch.float64, requires_grad=True)
     hs = torch.tensor(HS, dtype=torch.float64, requires_grad=True)
-    r = bd.binding.simulate(Wi, hs, NC, r0, noise, dt=DT)
+    r = bd.binding.simulate(Wi, hs, NC, r0, noise, dt=DT, scheme=SCHEME)
     off = np.concatenate([[0], np.cumsum(NC)])
     J = sum((r[off[c + 1] - 1] - r[off[c]]).norm() / (N - 1) for c, N in enumerate(NC)) / len(NC)
     J.backward()
-    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI)
+    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=SCHEME)
     _, dJdr = stretch_and_grad(r.detach().cpu().numpy(), NC)
     gw, gh = ctx.adjoint(r0, noise, torch.from_numpy(dJdr).cuda())
     ctx.close()

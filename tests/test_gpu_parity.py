@@ -100,13 +100,46 @@ def test_brownian_and_mobility_match_oracle(bd):
     ctx.close()
 
 
+# ------------------------------------------------------ midpoint stage
+@pytest.mark.parametrize("prec", [0, 1])
+def test_midpoint_stage_matches_oracle(bd, prec):
+    """r_m = r + P y / 2 and the step's displacement s D(r_m) L^{-T} xi of the
+    midpoint scheme, against the oracle's projection, back substitution,
+    assembly at r_m and product.  FP64 path to round-off; mixed path: r_m
+    within the factor's first-order error of the FP64 value (it projects the
+    refined displacement), the displacement within that error too."""
+    Nc = RAGGED if prec == 0 else [2, 43, 300, 1000]
+    ctx, r0 = make(bd, Nc, seed=19, dt=1e-4, precision=prec)
+    ctx.assemble()
+    ctx.factor()
+    tot = int(np.sum(Nc))
+    xi = inputs.gaussian_noise(1, tot, 20)[0]
+    rm, y = ctx.midpoint(cuda(xi))
+    rm, y = rm.cpu().numpy(), y.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(Nc)])
+    s = np.sqrt(2e-4)
+    for c in range(len(Nc)):
+        sl = slice(off[c], off[c + 1])
+        D = orc.assemble(r0[sl], 0.25, 0.25)
+        L, _ = orc.cholesky(D)
+        yB = s * orc.trmv_lower(L, xi[sl].ravel())
+        z = orc.trsv_lower_t(L, xi[sl].ravel())
+        rm_ref = r0[sl] + 0.5 * orc.tangent_project(r0[sl], yB)
+        y_ref = s * orc.gemv(orc.assemble(rm_ref, 0.25, 0.25), z)
+        tol_r, tol_y = (1e-14, 1e-13) if prec == 0 else (1e-3, 1e-3)
+        np.testing.assert_allclose(rm[sl], rm_ref, rtol=0, atol=tol_r * np.abs(yB).max() + 1e-15)
+        np.testing.assert_allclose(y[sl].ravel(), y_ref, rtol=0, atol=tol_y * np.abs(y_ref).max())
+    ctx.close()
+
+
 # ------------------------------------------------------------- full step
 def run_both(bd, Nc, steps, seed, **phys):
     Nc = np.asarray(Nc, np.int32)
     r0 = inputs.random_walk(Nc, seed)
     noise = inputs.gaussian_noise(steps, int(Nc.sum()), seed + 1)
     kw = dict(h_star=phys.get("hstar", 0.25), dt=phys.get("dt", 1e-4), flow=phys.get("flow", 0),
-              Wi=phys.get("Wi", 0.0), tol=phys.get("tol", 1e-13), max_newton=phys.get("max_newton", 50))
+              Wi=phys.get("Wi", 0.0), tol=phys.get("tol", 1e-13), max_newton=phys.get("max_newton", 50),
+              scheme=phys.get("scheme", 0))
     ctx = bd.Context(Nc, **kw)
     ctx.set_state(cuda(r0))
     ctx.step(cuda(noise))
@@ -116,7 +149,7 @@ def run_both(bd, Nc, steps, seed, **phys):
     launches = ctx.kernel_launches()
     ctx.close()
     p = orc.make_params(hstar=kw["h_star"], dt=kw["dt"], flow=kw["flow"], Wi=kw["Wi"],
-                        tol=kw["tol"], max_newton=kw["max_newton"])
+                        tol=kw["tol"], max_newton=kw["max_newton"], scheme=kw["scheme"])
     r_ref, T_ref, st_ref, it_ref, md_ref = orc.run(p, Nc, r0, noise)
     return r0, r_gpu, r_ref, st, st_ref, obs.cpu().numpy(), T_gpu, T_ref, launches
 
@@ -125,19 +158,23 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1.0)
 
 
-def test_step_parity_single_chain_n16_100_steps(bd):
-    """One chain of 16 beads at equilibrium (no flow), dt = 1e-4, 100 steps."""
-    r0, rg, rr, st, str_, obs, Tg, Tr, nl = run_both(bd, [16], 100, 1235)
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_step_parity_single_chain_n16_100_steps(bd, scheme):
+    """One chain of 16 beads at equilibrium (no flow), dt = 1e-4, 100 steps
+    (midpoint and Euler rigid-rod steps)."""
+    r0, rg, rr, st, str_, obs, Tg, Tr, nl = run_both(bd, [16], 100, 1235, scheme=scheme)
     assert (st == 0).all() and (str_ == 0).all()
     assert rel(rg, rr) < 1e-10
     assert obs[0, 6] < 1e-10      # rod lengths held
     assert nl > 0
 
 
-def test_step_parity_batch_n100_uniaxial(bd):
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_step_parity_batch_n100_uniaxial(bd, scheme):
     """8 chains of 100 beads, uniaxial extension Wi = 10, 100 steps; the
     observables (Eqs. (25)-(29)) against the oracle's on the oracle's state."""
-    r0, rg, rr, st, str_, obs, Tg, Tr, nl = run_both(bd, [100] * 8, 100, 1236, flow=2, Wi=10.0)
+    r0, rg, rr, st, str_, obs, Tg, Tr, nl = run_both(bd, [100] * 8, 100, 1236, flow=2, Wi=10.0,
+                                                     scheme=scheme)
     assert (st == 0).all() and (str_ == 0).all()
     assert rel(rg, rr) < 1e-10
     assert obs[:, 6].max() < 1e-10

@@ -10,6 +10,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2208_06559_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +39,10 @@ def test_static_matches_context_product_two_calls(bd, N, hs, a):
         torch.cuda.synchronize()
         err = (u - u_ref).abs().max().item() / max(u_ref.abs().max().item(), 1.0)
         assert err < 1e-13, (call, err)
+        # and against the FP64 oracle's assembled D times f
+        u_orc = orc.gemv(orc.assemble(r.cpu().numpy(), hs, a), f.cpu().numpy().ravel())
+        np.testing.assert_allclose(u.cpu().numpy().ravel(), u_orc, rtol=0,
+                                   atol=1e-13 * max(np.abs(u_orc).max(), 1.0))
     ctx.close()
 
 
@@ -52,3 +57,8 @@ def test_static_rejects_oversize_and_bad_args(bd):
     assert L.bd_mobility_apply_static(p(r), 0, 0.25, 0.0, p(f), p(u), None) == bd.binding.BD_ERR_ARG
     assert L.bd_mobility_apply_static(p(r), 10, 0.5, 0.25, p(f), p(u), None) == bd.binding.BD_ERR_ARG
     assert L.bd_mobility_apply_static(None, 10, 0.25, 0.0, p(f), p(u), None) == bd.binding.BD_ERR_ARG
+    assert L.bd_mobility_apply_static(p(r), 10, float("inf"), 0.0, p(f), p(u), None) == bd.binding.BD_ERR_ARG
+    assert L.bd_mobility_apply_static(p(r), 10, 0.25, float("inf"), p(f), p(u), None) == bd.binding.BD_ERR_ARG
+    assert L.bd_mobility_apply_static(p(r), 10, float("nan"), 0.0, p(f), p(u), None) == bd.binding.BD_ERR_ARG
+    host = torch.zeros((10, 3), dtype=torch.float64)   # host memory is not the current device's
+    assert L.bd_mobility_apply_static(p(host), 10, 0.25, 0.0, p(f), p(u), None) == bd.binding.BD_ERR_ARG
