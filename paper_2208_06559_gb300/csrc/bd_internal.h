@@ -191,6 +191,18 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
                                 bool refine, double* y, double* y1, double* z, double* w,
                                 double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
                                 cudaEvent_t* ev, bool need_z = false);
+// The same in two parts.  begin: the noise split, the triangular solve forked
+// to s2 (z = B^{-T} xi, unscaled, when refine or need_z), and the product
+// B xi on s -- into y1 unscaled when refine, else into y scaled; end: the
+// join, then (refine) the product D z and y = s/2 (y1 + D z).
+cudaError_t launch_brownian_f32_begin(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
+                                      int max_np, const double* x, const StepArgs* args, double scale,
+                                      bool refine, double* y, double* y1, double* z, double* scratch,
+                                      cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev, bool need_z);
+cudaError_t launch_brownian_f32_end(const float* M, const ChainDesc* cd, int n_chains, int max_np, double scale,
+                                    bool refine, double* y, const double* y1, const double* z, double* w,
+                                    double* scratch, float2* fsplit, cudaStream_t s, cudaEvent_t* ev,
+                                    bool need_z);
 
 // Midpoint corrector of the rigid-rod step (k_midpoint.cu).
 // r_m = r + P y / 2 (P: orthogonal projection onto the tangent space of the

@@ -72,7 +72,7 @@ struct bd_ctx {
   cudaStream_t gs[kMaxGroups] = {};
   cudaEvent_t gev[kMaxGroups + 1] = {};
   // concurrent branches of the step: the K chain, the refinement's solve
-  cudaStream_t aux[2] = {};
+  cudaStream_t aux[3] = {};  // [0] K chain (low priority), [1] refinement solve, [2] midpoint K chain
   cudaEvent_t aev[7] = {};  // [0,1] K-chain fork/join, [2,3] refinement fork/join, [4,5] caller-stream fence,
                             // [6] mixed: rod directions and G formed
   cudaGraph_t graph = nullptr;
@@ -90,7 +90,6 @@ struct bd_ctx {
   bool midpoint = false;        // rigid rods, BD_SCHEME_MIDPOINT: mobility and rod directions at r_m
   double* rmid = nullptr;       // midpoint positions r_m, [sum N][3]
   double* umid = nullptr;       // unit rod directions of r_m, [sum (N-1)][3]
-  double* rK = nullptr;         // mixed midpoint path: positions at which K is formed, [sum N][3]
   void* M2 = nullptr;           // FP64 midpoint path: D(r_m), full symmetric, layout of M
   std::mutex mu;
 };
@@ -192,7 +191,7 @@ void prof_mark(bd_ctx* c, int i, cudaStream_t s) {
 // the directions of r_m, its factor) beside the product y = D(r_m) z.
 int enqueue_pre_newton_mid_fp64(bd_ctx* c, cudaStream_t s) {
   int rc;
-  cudaStream_t sk = c->aux[0];
+  cudaStream_t sk = c->aux[2];
   if ((rc = enqueue_assemble(c, s))) return rc;
   prof_mark(c, 1, s);
   if ((rc = enqueue_factor(c, s))) return rc;
@@ -220,43 +219,43 @@ int enqueue_pre_newton_mid_fp64(bd_ctx* c, cudaStream_t s) {
   return BD_OK;
 }
 
-// Midpoint step, mixed path.  The K chain preconditions the tension
-// iteration and runs beside the factorisation as in the Euler step (the
-// root of the iteration does not depend on it): K is formed at an estimate
-// of the midpoint that needs no factor, r + P (s xi) / 2 (the Brownian
-// displacement without HI), with that estimate's rod directions, then
-// factored with its super-block inverses.  The main chain: D and its
-// tensor-core factor at r, the refined y and z = Lt^{-T} xi (in F), r_m and
-// its rod directions, y += s (D(r_m) - D(r)) z from the positions, G of r_m,
-// the predictor.
+// Midpoint step, mixed path.  D and its tensor-core factor at r; the product
+// Lt xi (the raw displacement s Lt xi places the midpoint: its correlation
+// with z = Lt^{-T} xi is exactly s^2 I) while the solve for z runs beside it;
+// r_m and its rod directions; then the K chain (K and G of r_m, K's factor
+// and super-block inverses) on its own high-priority stream, beside the
+// refinement's product D z, y += s (D(r_m) - D(r)) z from the positions and
+// the predictor.  The first tension product waits for G, the first solve for
+// the end of the K chain.
 int enqueue_pre_newton_mid_mixed(bd_ctx* c, cudaStream_t s) {
   int rc;
-  cudaStream_t sk = c->aux[0];
-  CK(cudaEventRecord(c->aev[0], s));
-  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  cudaStream_t sk = c->aux[2];
+  const bool refine = c->p.refine != 0;
   if ((rc = enqueue_assemble(c, s))) return rc;
   prof_mark(c, 1, s);
-  CK(launch_tangent_midpoint(c->r, nullptr, c->args, c->ph.sq2dt, c->d_cd, c->n_chains, c->status, c->rK,
-                             c->uhat, sk));
-  CK(launch_form_k_pos(c->rK, (float*)c->K, nullptr, c->d_cd, c->n_chains, c->max_m, c->uhat, c->ph.hstar,
+  if ((rc = enqueue_factor(c, s))) return rc;
+  prof_mark(c, 2, s);
+  CK(launch_brownian_f32_begin((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, nullptr, c->args,
+                               c->ph.sq2dt, refine, c->y, c->rT, c->F, c->scratch, s, c->aux[1], c->aev + 2, true));
+  CK(launch_tangent_midpoint(c->r, refine ? c->rT : c->y, nullptr, refine ? c->ph.sq2dt : 1.0, c->d_cd,
+                             c->n_chains, c->status, c->rmid, c->umid, s));
+  CK(cudaEventRecord(c->aev[0], s));
+  CK(cudaStreamWaitEvent(sk, c->aev[0], 0));
+  CK(launch_form_k_pos(c->rmid, (float*)c->K, c->G, c->d_cd, c->n_chains, c->max_m, c->umid, c->ph.hstar,
                        c->ph.a, sk));
+  CK(cudaEventRecord(c->aev[6], sk));
   CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64, c->status, sk));
   CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
   prof_mark(c, 7, sk);
   CK(cudaEventRecord(c->aev[1], sk));
-  if ((rc = enqueue_factor(c, s))) return rc;
-  prof_mark(c, 2, s);
-  CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, nullptr, c->args,
-                         c->ph.sq2dt, c->p.refine != 0, c->y, c->rT, c->F, c->u, c->scratch, c->fsplit, s,
-                         c->aux[1], c->aev + 2, true));
-  CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+  CK(launch_brownian_f32_end((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->ph.sq2dt, refine, c->y,
+                             c->rT, c->F, c->u, c->scratch, c->fsplit, s, c->aev + 2, true));
   CK(launch_mob_delta_f32(c->r, c->rmid, c->F, c->d_cd, c->n_chains, c->max_N, c->status, c->ph.hstar, c->ph.a,
                           c->ph.sq2dt, c->y, s));
-  CK(launch_form_k_pos(c->rmid, nullptr, c->G, c->d_cd, c->n_chains, c->max_m, c->umid, c->ph.hstar, c->ph.a,
-                       s));
   prof_mark(c, 3, s);
   CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->umid, c->T, c->F,
                       c->state, c->status, c->iters, c->accurate, s));
+  CK(cudaStreamWaitEvent(s, c->aev[6], 0));  // G of r_m, for the first product
   prof_mark(c, 4, s);
   return BD_OK;
 }
@@ -382,7 +381,8 @@ void set_graph_priorities(bd_ctx* c, cudaGraph_t g) {
     if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
-    const bool kchain = c->mixed && (kp.func == rod_dirs_kernel() ||
+    // (the midpoint step's K chain is on the critical path: high priority)
+    const bool kchain = c->mixed && !c->midpoint && (kp.func == rod_dirs_kernel() ||
                                      is_k64_kernel(kp.func) || is_kchain_form_kernel(kp.func) ||
                                      is_sb_inverse_kernel(kp.func));
     cudaLaunchAttributeValue v;
@@ -642,14 +642,14 @@ void bd_destroy(bd_ctx* c) {
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
                   c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
-                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2, c->rK};
+                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
     if (c->gs[g]) cudaStreamDestroy(c->gs[g]);
   for (int g = 0; g <= bd_ctx::kMaxGroups; ++g)
     if (c->gev[g]) cudaEventDestroy(c->gev[g]);
-  for (int g = 0; g < 2; ++g)
+  for (int g = 0; g < 3; ++g)
     if (c->aux[g]) cudaStreamDestroy(c->aux[g]);
   for (int g = 0; g < 7; ++g)
     if (c->aev[g]) cudaEventDestroy(c->aev[g]);
@@ -797,7 +797,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
          alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (2 * c->n_chains + 1));
   if (ok && c->midpoint)
     ok = alloc((void**)&c->rmid, b3) && alloc((void**)&c->umid, 3 * rr) &&
-         (c->mixed ? alloc((void**)&c->rK, b3) : alloc(&c->M2, c->M_elems * sizeof(double)));
+         (c->mixed || alloc(&c->M2, c->M_elems * sizeof(double)));
   if (!ok) {
     bd_destroy(c);
     return BD_ERR_OOM;
@@ -818,7 +818,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (cudaStreamCreateWithPriority(&c->cs, cudaStreamNonBlocking, pr_high) != cudaSuccess ||
       cudaStreamCreateWithPriority(&c->cs2, cudaStreamNonBlocking, pr_high) != cudaSuccess ||
       cudaStreamCreateWithPriority(&c->aux[0], cudaStreamNonBlocking, pr_low) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, pr_high) != cudaSuccess)
+      cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, pr_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->aux[2], cudaStreamNonBlocking, pr_high) != cudaSuccess)
     return fail(BD_ERR_CUDA);
   for (int g = 0; g < 7; ++g)
     if (cudaEventCreateWithFlags(&c->aev[g], cudaEventDisableTiming) != cudaSuccess)
@@ -1052,10 +1053,14 @@ int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (c->mixed) {
-    CK(launch_brownian_f32((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, xi_dev, nullptr,
-                           c->ph.sq2dt, c->p.refine != 0, c->y, c->rT, c->F, c->u, c->scratch, c->fsplit, s,
-                           c->aux[1], c->aev + 2, true));
-    CK(launch_tangent_midpoint(c->r, c->y, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid, s));
+    const bool refine = c->p.refine != 0;
+    CK(launch_brownian_f32_begin((const float*)c->M, c->Winv, c->d_cd, c->n_chains, c->max_np, xi_dev, nullptr,
+                                 c->ph.sq2dt, refine, c->y, c->rT, c->F, c->scratch, s, c->aux[1], c->aev + 2,
+                                 true));
+    CK(launch_tangent_midpoint(c->r, refine ? c->rT : c->y, nullptr, refine ? c->ph.sq2dt : 1.0, c->d_cd,
+                               c->n_chains, c->status, c->rmid, c->umid, s));
+    CK(launch_brownian_f32_end((const float*)c->M, c->d_cd, c->n_chains, c->max_np, c->ph.sq2dt, refine, c->y,
+                               c->rT, c->F, c->u, c->scratch, c->fsplit, s, c->aev + 2, true));
     CK(launch_mob_delta_f32(c->r, c->rmid, c->F, c->d_cd, c->n_chains, c->max_N, c->status, c->ph.hstar,
                             c->ph.a, c->ph.sq2dt, c->y, s));
   } else {

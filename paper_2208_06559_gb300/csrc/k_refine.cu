@@ -272,11 +272,10 @@ __global__ void k_refine_combine(const ChainDesc* __restrict__ cd, const double*
   y[o] = half_scale * (y1[o] + w[o]);
 }
 
-cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
-                                int max_np, const double* x, const StepArgs* args, double scale,
-                                bool refine, double* y, double* y1, double* z, double* w,
-                                double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
-                                cudaEvent_t* ev, bool need_z) {
+cudaError_t launch_brownian_f32_begin(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
+                                      int max_np, const double* x, const StepArgs* args, double scale,
+                                      bool refine, double* y, double* y1, double* z, double* scratch,
+                                      cudaStream_t s, cudaStream_t s2, cudaEvent_t* ev, bool need_z) {
   k_split<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, x, args, scratch);
   if (!refine && !need_z) {
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
@@ -292,13 +291,33 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
   else
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, scale, y);
   e = cudaEventRecord(ev[1], s2);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e != cudaSuccess) return e;
-  if (!refine) return cudaGetLastError();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_brownian_f32_end(const float* M, const ChainDesc* cd, int n_chains, int max_np, double scale,
+                                    bool refine, double* y, const double* y1, const double* z, double* w,
+                                    double* scratch, float2* fsplit, cudaStream_t s, cudaEvent_t* ev,
+                                    bool need_z) {
+  if (!refine && !need_z) return cudaSuccess;
+  cudaError_t e = cudaStreamWaitEvent(s, ev[1], 0);
+  if (e != cudaSuccess || !refine) return e;
   e = launch_symv_f32(M, cd, n_chains, max_np, z, fsplit, scratch, w, nullptr, s);
   if (e != cudaSuccess) return e;
   k_refine_combine<<<dim3(ceil_div(max_np, 256), n_chains), 256, 0, s>>>(cd, y1, w, 0.5 * scale, y);
   return cudaGetLastError();
+}
+
+cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDesc* cd, int n_chains,
+                                int max_np, const double* x, const StepArgs* args, double scale,
+                                bool refine, double* y, double* y1, double* z, double* w,
+                                double* scratch, float2* fsplit, cudaStream_t s, cudaStream_t s2,
+                                cudaEvent_t* ev, bool need_z) {
+  cudaError_t e = launch_brownian_f32_begin(M, Winv, cd, n_chains, max_np, x, args, scale, refine, y, y1, z,
+                                            scratch, s, s2, ev, need_z);
+  if (e != cudaSuccess) return e;
+  return launch_brownian_f32_end(M, cd, n_chains, max_np, scale, refine, y, y1, z, w, scratch, fsplit, s, ev,
+                                 need_z);
 }
 
 cudaError_t refine_configure() {
