@@ -221,8 +221,10 @@ int bd_midpoint(bd_ctx* ctx, const double* xi_dev, double* rmid_dev, double* y_d
  * L' = L Phi(L^{-1} D' L^{-T}), of the Brownian and flow terms, and of the
  * tension solve by the implicit function theorem), which for two parameters
  * needs no checkpoints; ckpt_every is accepted and ignored.  The context is
- * left at the final state.  FP64 contexts with h* > 0 and BD_SCHEME_EULER
- * only (else BD_ERR_ARG).
+ * left at the final state.  With BD_SCHEME_MIDPOINT the tangents also run
+ * through the midpoint: z' = -L^{-T} Phi(X)^T xi, the derivative of the
+ * tangent-space projection, and D(r_m)' from r_m'.  FP64 rigid-rod contexts
+ * with h* > 0 only (else BD_ERR_ARG).
  * Synchronises the stream; returns the most severe chain status. */
 int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noise_dev,
                int ckpt_every, const double* dJdr_final_dev, double grad_host[2], void* stream);

@@ -391,7 +391,7 @@ class Context:
 
 def simulate(Wi, h_star, n_beads, r0, noise, dt: float = 1e-4, flow: int = FLOW_UNIAXIAL,
              lam: float = 1.0, tol: float = 1e-13, max_newton: int = 50, ckpt_every: int = 20,
-             scheme: int = SCHEME_EULER):
+             scheme: int = SCHEME_MIDPOINT):
     """Final positions after noise.shape[0] FP64 steps from r0, differentiable
     with respect to the 0-dim float64 tensors Wi and h_star (a = h_star).
 

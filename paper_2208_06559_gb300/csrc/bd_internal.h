@@ -245,10 +245,22 @@ cudaError_t launch_phi_matvec(const double* X, const ChainDesc* cd, int n_chains
                               const double* xi, double* v, cudaStream_t s);
 cudaError_t launch_gemv_dense(const double* A, const ChainDesc* cd, int n_chains, int max_n,
                               const double* f, double* w, cudaStream_t s);
-cudaError_t launch_tangent_predictor(const double* r, const double* rdot, const double* ydot,
-                                     const double* uhat, const double* T, const ChainDesc* cd,
+// r*' and G = C(T u'); the rod directions and their tangents from (rq, rqdot).
+cudaError_t launch_tangent_predictor(const double* r, const double* rdot, const double* rq, const double* rqdot,
+                                     const double* ydot, const double* uhat, const double* T, const ChainDesc* cd,
                                      int n_chains, int max_N, Phys ph, const double* kappa_dot,
                                      double* rsdot, double* G, cudaStream_t s);
+// v = Phi(X)^T xi for symmetric X (strict upper triangle plus half the diagonal).
+cudaError_t launch_phi_upper_matvec(const double* X, const ChainDesc* cd, int n_chains, int max_n,
+                                    const double* xi, double* v, cudaStream_t s);
+// r_m' = r' + (P y)' / 2, the tangent of the midpoint of the corrected step.
+cudaError_t launch_tangent_midpoint_dot(const double* r, const double* rdot, const double* y, const double* ydot,
+                                        const ChainDesc* cd, int n_chains, const int* status, double* rmdot,
+                                        cudaStream_t s);
+cudaError_t tangent_configure();
+// out = a + b over every chain's 3N values.
+cudaError_t launch_vec_add(const ChainDesc* cd, int n_chains, int max_n, const double* a, const double* b,
+                           double* out, cudaStream_t s);
 cudaError_t launch_tangent_base(const ChainDesc* cd, int n_chains, int max_n, Phys ph,
                                 const double* rsdot, const double* DdF, const double* DG, double* a,
                                 cudaStream_t s);

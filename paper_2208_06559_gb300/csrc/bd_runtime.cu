@@ -81,6 +81,8 @@ struct bd_ctx {
   double *Md = nullptr, *rdot = nullptr, *ydot = nullptr, *rsdot = nullptr, *Gt = nullptr;
   double *abase = nullptr, *zt = nullptr, *DdF = nullptr, *DG = nullptr, *vt = nullptr;
   double *Tdot = nullptr, *Fdot = nullptr, *rscale = nullptr, *kdot = nullptr;
+  // midpoint step: y at r, s z, the midpoint's tangent, Phi(X)^T xi, z's tangent
+  double *yB = nullptr, *zsv = nullptr, *rmdot = nullptr, *v2 = nullptr, *zdot = nullptr;
   bool have_state = false;
   int direct_iters = 0;  // > 0: launch the step's kernels directly (profiling), no graph
   int graph_unroll = 0;  // tension iterations captured as plain graph nodes before the WHILE node
@@ -642,7 +644,7 @@ void bd_destroy(bd_ctx* c) {
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
                   c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
-                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2};
+                  c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2, c->yB, c->zsv, c->rmdot, c->v2, c->zdot};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < bd_ctx::kMaxGroups; ++g)
@@ -844,7 +846,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
       assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
       k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess ||
-      solve_sb_configure() != cudaSuccess || midpoint_configure() != cudaSuccess)
+      solve_sb_configure() != cudaSuccess || midpoint_configure() != cudaSuccess ||
+      tangent_configure() != cudaSuccess)
     return fail(BD_ERR_CUDA);
   if (cudaMemcpyAsync(c->d_cd, c->h_cd.data(), sizeof(ChainDesc) * c->n_chains,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1084,7 +1087,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
                const double* dJdr_final_dev, double grad_host[2], void* stream) {
   (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
   if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
-  if (c->mixed || c->fraenkel || c->midpoint || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
+  if (c->mixed || c->fraenkel || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1102,6 +1105,9 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
           al(&c->Gt, b3) && al(&c->abase, b3) && al(&c->zt, b3) && al(&c->DdF, b3) && al(&c->DG, b3) &&
           al(&c->vt, b3) && al(&c->Tdot, nr) && al(&c->Fdot, b3) && al(&c->rscale, c->n_chains) &&
           al(&c->kdot, 18)))
+      return BD_ERR_OOM;
+    if (c->midpoint && !(al(&c->yB, b3) && al(&c->zsv, b3) && al(&c->rmdot, b3) && al(&c->v2, b3) &&
+                         al(&c->zdot, b3)))
       return BD_ERR_OOM;
     CK(cudaMemsetAsync(c->Md, 0, c->M_elems * sizeof(double), s));
   }
@@ -1124,6 +1130,11 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
   const int tiles = c->max_np / kSimtTile;
   const int iters_max = c->ph.max_newton + 2;
   int rc;
+  const bool mid = c->midpoint;
+  // the mobility, rod directions and their positions the tension solve uses
+  const void* Mt = mid ? c->M2 : c->M;
+  const double* udir = mid ? c->umid : c->uhat;
+  const size_t b3b = b3 * sizeof(double);
   for (int step = 0; step < n_steps; ++step) {
     const double* xi = noise_dev + (size_t)step * b3;
     // ---- primal step, intermediates kept (r still holds the old positions)
@@ -1131,27 +1142,40 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
     if ((rc = enqueue_factor(c, s))) return rc;
     CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, xi, nullptr, c->ph.sq2dt,
                            c->y, s));
-    CK(launch_rod_dirs(c->r, c->d_cd, c->n_chains, c->max_N, c->uhat, s));
-    CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
-                             c->uhat, s));
+    if (mid) {
+      CK(cudaMemcpyAsync(c->yB, c->y, b3b, cudaMemcpyDeviceToDevice, s));
+      CK(launch_trsv_t_f64((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, c->max_n, xi,
+                           nullptr, c->ph.sq2dt, c->zsv, s));
+      CK(launch_tangent_midpoint(c->r, c->yB, nullptr, 1.0, c->d_cd, c->n_chains, c->status, c->rmid, c->umid,
+                                 s));
+      CK(launch_assemble<double>(c->rmid, (double*)c->M2, c->d_cd, c->n_chains, c->max_N, c->max_np,
+                                 c->ph.hstar, c->ph.a, nullptr, s));
+      CK(launch_form_k<double>((const double*)c->M2, (double*)c->K, c->d_cd, c->n_chains, c->max_m, c->umid, s));
+      if ((rc = enqueue_symv(c, c->M2, c->zsv, c->y, nullptr, s))) return rc;
+    } else {
+      CK(launch_rod_dirs(c->r, c->d_cd, c->n_chains, c->max_N, c->uhat, s));
+      CK(launch_form_k<double>((const double*)c->M, (double*)c->K, c->d_cd, c->n_chains, c->max_m,
+                               c->uhat, s));
+    }
     CK(launch_chol_simt<double>((double*)c->K, (double*)c->Kinv, c->d_cd, c->n_chains,
                                 c->max_mp / kSimtTile, true, c->status, s));
-    CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, c->uhat, c->T,
+    CK(launch_predictor(c->r, c->y, c->d_cd, c->n_chains, c->max_N, c->ph, c->rstar, udir, c->T,
                         c->F, c->state, c->status, c->iters, nullptr, s));
     for (int it = 0; it < iters_max; ++it) {
-      if ((rc = enqueue_symv(c, c->M, c->F, c->u, c->state, s))) return rc;
+      if ((rc = enqueue_symv(c, Mt, c->F, c->u, c->state, s))) return rc;
       CK(launch_newton_residual(c->rstar, c->u, c->d_cd, c->n_chains, c->ph, c->rT, c->rhs, c->state,
                                 c->status, c->iters, s));
       CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
-                                     c->ph, c->uhat, c->rhs, c->T, c->F, c->state, c->iters, s));
+                                     c->ph, udir, c->rhs, c->T, c->F, c->state, c->iters, s));
     }
     // ---- tangents for p = Wi (0) and p = h* (1)
     for (int p = 0; p < 2; ++p) {
       double* rd = c->rdot + (size_t)p * b3;
       const double hdot = (p == 1) ? 1.0 : 0.0, adot = (p == 1 && tied) ? 1.0 : 0.0;
+      // X = L^{-1} D' L^{-T} in Md; y' = s L Phi(X) xi
       CK(launch_assemble_dot(c->r, rd, c->d_cd, c->n_chains, c->max_N, c->Md, c->ph.hstar, c->ph.a, hdot,
                              adot, s));
-      CK(launch_gemv_dense(c->Md, c->d_cd, c->n_chains, c->max_n, c->F, c->DdF, s));
+      if (!mid) CK(launch_gemv_dense(c->Md, c->d_cd, c->n_chains, c->max_n, c->F, c->DdF, s));
       CK(launch_trsm_rhs((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, tiles, c->Md,
                          s));
       CK(launch_transpose(c->d_cd, c->n_chains, tiles, c->Md, s));
@@ -1160,18 +1184,35 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
       CK(launch_phi_matvec(c->Md, c->d_cd, c->n_chains, c->max_n, xi, c->vt, s));
       CK(launch_trmv<double>((const double*)c->M, c->d_cd, c->n_chains, c->max_n, c->vt, nullptr,
                              c->ph.sq2dt, c->ydot, s));
-      CK(launch_tangent_predictor(c->r, rd, c->ydot, c->uhat, c->T, c->d_cd, c->n_chains, c->max_N, c->ph,
+      const double* rq = c->r;
+      const double* rqd = rd;
+      if (mid) {
+        // (s z)' = -s L^{-T} Phi(X)^T xi; r_m'; D_m' in Md; noise part s (D_m' z + D_m z')
+        CK(launch_phi_upper_matvec(c->Md, c->d_cd, c->n_chains, c->max_n, xi, c->v2, s));
+        CK(launch_trsv_t_f64((const double*)c->M, (const double*)c->Minv, c->d_cd, c->n_chains, c->max_n,
+                             c->v2, nullptr, -c->ph.sq2dt, c->zdot, s));
+        CK(launch_tangent_midpoint_dot(c->r, rd, c->yB, c->ydot, c->d_cd, c->n_chains, c->status, c->rmdot, s));
+        CK(launch_assemble_dot(c->rmid, c->rmdot, c->d_cd, c->n_chains, c->max_N, c->Md, c->ph.hstar, c->ph.a,
+                               hdot, adot, s));
+        CK(launch_gemv_dense(c->Md, c->d_cd, c->n_chains, c->max_n, c->F, c->DdF, s));
+        CK(launch_gemv_dense(c->Md, c->d_cd, c->n_chains, c->max_n, c->zsv, c->vt, s));
+        if ((rc = enqueue_symv(c, c->M2, c->zdot, c->DG, nullptr, s))) return rc;
+        CK(launch_vec_add(c->d_cd, c->n_chains, c->max_n, c->vt, c->DG, c->ydot, s));
+        rq = c->rmid;
+        rqd = c->rmdot;
+      }
+      CK(launch_tangent_predictor(c->r, rd, rq, rqd, c->ydot, udir, c->T, c->d_cd, c->n_chains, c->max_N, c->ph,
                                   c->kdot + 9 * p, c->rsdot, c->Gt, s));
-      if ((rc = enqueue_symv(c, c->M, c->Gt, c->DG, nullptr, s))) return rc;
+      if ((rc = enqueue_symv(c, Mt, c->Gt, c->DG, nullptr, s))) return rc;
       CK(launch_tangent_base(c->d_cd, c->n_chains, c->max_n, c->ph, c->rsdot, c->DdF, c->DG, c->abase, s));
       CK(launch_tangent_init(c->d_cd, c->n_chains, c->max_n, c->status, c->state, c->iters, c->Tdot,
                              c->Fdot, s));
       for (int it = 0; it < iters_max; ++it) {
-        if ((rc = enqueue_symv(c, c->M, c->Fdot, c->u, c->state, s))) return rc;
+        if ((rc = enqueue_symv(c, Mt, c->Fdot, c->u, c->state, s))) return rc;
         CK(launch_tangent_residual(c->abase, c->u, c->rT, c->d_cd, c->n_chains, c->ph, 1e-12, c->rscale,
                                    c->zt, c->rhs, c->state, c->status, c->iters, s));
         CK(launch_newton_solve<double>((const double*)c->K, (const double*)c->Kinv, c->d_cd, c->n_chains,
-                                       c->ph, c->uhat, c->rhs, c->Tdot, c->Fdot, c->state, c->iters, s));
+                                       c->ph, udir, c->rhs, c->Tdot, c->Fdot, c->state, c->iters, s));
       }
       CK(cudaMemcpyAsync(rd, c->zt, b3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }

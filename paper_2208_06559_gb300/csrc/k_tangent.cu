@@ -16,6 +16,14 @@
 //   T' from  2 Q_k . Delta[r*' + dt D' F + dt D C(T u') + dt D C(T' u)]_k = 0,
 //   solved by the same K-preconditioned iteration as the tensions,
 //   r_new' = r*' + dt D' F + dt D C(T u') + dt D C(T' u).
+// The midpoint step (mobility and rod directions at r_m = r + P y / 2, the
+// Brownian displacement s D(r_m) z with z = L^{-T} xi) adds
+//   z'   = -L^{-T} Phi(X)^T xi          (from L^T z = xi and L' = L Phi(X)),
+//   (P y)' = y' - (A^T x)',  (A A^T) x = A y,
+//            (A A^T) x' = (A y)' - (A A^T)' x  (A from the unit rods of r),
+//   r_m' = r' + (P y)' / 2,  D_m' from r_m and r_m' (dual numbers),
+//   the Brownian part s (D_m' z + D_m z'),
+// and the tension part above with D_m, D_m' and the rod directions of r_m.
 // The paper has no derivatives; these kernels serve bd_adjoint.
 #include <math.h>
 
@@ -193,6 +201,24 @@ __global__ void __launch_bounds__(256) k_phi_matvec(const double* __restrict__ X
   if (lane == 0) v[3 * d.boff + row] = s;
 }
 
+// v = Phi(X)^T xi for symmetric X: v_i = sum_{j > i} X_ij xi_j + X_ii xi_i / 2.
+__global__ void __launch_bounds__(256) k_phi_upper_matvec(const double* __restrict__ X,
+                                                          const ChainDesc* __restrict__ cd,
+                                                          const double* __restrict__ xi,
+                                                          double* __restrict__ v) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= d.n) return;
+  const double* xr = X + d.moff + (long long)row * d.np;
+  const double* x = xi + 3 * d.boff;
+  double s = 0.0;
+  for (int c = row + lane; c < d.n; c += 32) s += (c == row ? 0.5 : 1.0) * xr[c] * x[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) v[3 * d.boff + row] = s;
+}
+
 // w = A f for a dense n x n block (pitch np) of every chain, warp per row.
 __global__ void __launch_bounds__(256) k_gemv_dense(const double* __restrict__ A,
                                                     const ChainDesc* __restrict__ cd,
@@ -213,7 +239,10 @@ __global__ void __launch_bounds__(256) k_gemv_dense(const double* __restrict__ A
 
 // r*' = r' + dt (kappa' r + kappa r') + y'  and  G = C(T u') (bead forces of
 // the rod-direction change), u'_k = (I - u u^T) Q'_k / |Q_k| (old positions).
+// The rod directions (and their tangents) come from rq, rqdot: the positions
+// of the start of the step (Euler) or the midpoint (midpoint step).
 __global__ void k_tangent_predictor(const double* __restrict__ r, const double* __restrict__ rdot,
+                                    const double* __restrict__ rq_, const double* __restrict__ rqdot,
                                     const double* __restrict__ ydot, const double* __restrict__ uhat,
                                     const double* __restrict__ T, const ChainDesc* __restrict__ cd,
                                     Phys ph, const double* __restrict__ kappa_dot,
@@ -230,8 +259,8 @@ __global__ void k_tangent_predictor(const double* __restrict__ r, const double* 
     rsdot[3 * (d.boff + i) + k] = s;
   }
   auto udot = [&](int kr, double out[3]) {
-    const double* a0 = r + 3 * (d.boff + kr);
-    const double* v0 = rdot + 3 * (d.boff + kr);
+    const double* a0 = rq_ + 3 * (d.boff + kr);
+    const double* v0 = rqdot + 3 * (d.boff + kr);
     const double q[3] = {a0[3] - a0[0], a0[4] - a0[1], a0[5] - a0[2]};
     const double qd[3] = {v0[3] - v0[0], v0[4] - v0[1], v0[5] - v0[2]};
     const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
@@ -330,6 +359,201 @@ __global__ void k_tangent_init(const ChainDesc* __restrict__ cd, const int* __re
   if (e < d.n) Fdot[3 * d.boff + e] = 0.0;
 }
 
+// ------------------------------------------------- midpoint tangent
+// One CTA per chain.  With u the unit rods of r, c = A y, H = A A^T
+// (tridiagonal: 2, -u_k . u_k+1), x = H^{-1} c:
+//   c'_k = u'_k . (y_k+1 - y_k) + u_k . (y'_k+1 - y'_k),
+//   H'_k,k+1 = -(u'_k . u_k+1 + u_k . u'_k+1),  H'_kk = 0,
+//   x' = H^{-1} (c' - H' x),
+//   (P y)'_i = y'_i + x'_i u_i + x_i u'_i - x'_{i-1} u_{i-1} - x_{i-1} u'_{i-1},
+// and r_m' = r' + (P y)' / 2.  The two solves share one cyclic reduction
+// (the same elimination factors for both right-hand sides).
+constexpr int kTmThreads = 1024;
+constexpr int kTmMaxP = 4096;
+
+__device__ __forceinline__ void rod_and_dot(const double* rc, const double* vc, int k, double u[3], double ud[3]) {
+  const double q[3] = {rc[3 * k + 3] - rc[3 * k], rc[3 * k + 4] - rc[3 * k + 1], rc[3 * k + 5] - rc[3 * k + 2]};
+  const double qd[3] = {vc[3 * k + 3] - vc[3 * k], vc[3 * k + 4] - vc[3 * k + 1], vc[3 * k + 5] - vc[3 * k + 2]};
+  const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) u[e] = q[e] / qn;
+  const double uq = u[0] * qd[0] + u[1] * qd[1] + u[2] * qd[2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) ud[e] = (qd[e] - u[e] * uq) / qn;
+}
+
+__global__ void __launch_bounds__(kTmThreads) k_tangent_midpoint_dot(const double* __restrict__ r,
+                                                                     const double* __restrict__ rdot,
+                                                                     const double* __restrict__ y,
+                                                                     const double* __restrict__ ydot,
+                                                                     const ChainDesc* __restrict__ cd,
+                                                                     const int* __restrict__ status,
+                                                                     double* __restrict__ rmdot) {
+  extern __shared__ __align__(16) double tmd_smem[];
+  const int c = blockIdx.x;
+  const ChainDesc d = cd[c];
+  const int N = d.N, m = d.m, t = threadIdx.x;
+  const long long b3 = 3 * d.boff;
+  const double *rc = r + b3, *vc = rdot + b3, *yc = y + b3, *ydc = ydot + b3;
+  double* out = rmdot + b3;
+  if (status[c] != BD_OK) {
+    for (int e = t; e < 3 * N; e += kTmThreads) out[e] = vc[e];
+    return;
+  }
+  int P = 1;
+  while (P < m) P <<= 1;
+  double* ca = tmd_smem;
+  double* cb = ca + P;
+  double* cc = cb + P;
+  double* x1 = cc + P;  // rhs c, then x
+  double* x2 = x1 + P;  // rhs c' - H' x, then x'
+  // pass 1: H and c; x by cyclic reduction (x2 unused yet)
+  for (int i = t; i < P; i += kTmThreads) {
+    double a = 0.0, cu = 0.0, rhs = 0.0;
+    if (i < m) {
+      double u[3], ud[3];
+      rod_and_dot(rc, vc, i, u, ud);
+      if (i > 0) {
+        double up[3], upd[3];
+        rod_and_dot(rc, vc, i - 1, up, upd);
+        a = -(up[0] * u[0] + up[1] * u[1] + up[2] * u[2]);
+      }
+      if (i + 1 < m) {
+        double un[3], und[3];
+        rod_and_dot(rc, vc, i + 1, un, und);
+        cu = -(u[0] * un[0] + u[1] * un[1] + u[2] * un[2]);
+      }
+      rhs = u[0] * (yc[3 * i + 3] - yc[3 * i]) + u[1] * (yc[3 * i + 4] - yc[3 * i + 1]) +
+            u[2] * (yc[3 * i + 5] - yc[3 * i + 2]);
+    }
+    ca[i] = a;
+    cb[i] = (i < m) ? 2.0 : 1.0;
+    cc[i] = cu;
+    x1[i] = rhs;
+    x2[i] = 0.0;
+  }
+  __syncthreads();
+  // The elimination runs twice: for x, then, once the right-hand side
+  // c' - H' x is formed, for x'.  It overwrites the coefficients, so they are
+  // formed again (load_h) before the second run.
+  auto solve = [&](double* rhs) {
+    for (int s = 1; s < P; s <<= 1) {
+      for (int i = 2 * s - 1 + 2 * s * t; i < P; i += 2 * s * kTmThreads) {
+        const int l = i - s, rr = i + s;
+        const double k1 = ca[i] / cb[l];
+        double nb = cb[i] - cc[l] * k1, nd = rhs[i] - rhs[l] * k1, nc = 0.0;
+        if (rr < P) {
+          const double k2 = cc[i] / cb[rr];
+          nb -= ca[rr] * k2;
+          nd -= rhs[rr] * k2;
+          nc = -cc[rr] * k2;
+        }
+        ca[i] = -ca[l] * k1;
+        cb[i] = nb;
+        cc[i] = nc;
+        rhs[i] = nd;
+      }
+      __syncthreads();
+    }
+    if (t == 0) rhs[P - 1] = rhs[P - 1] / cb[P - 1];
+    __syncthreads();
+    for (int s = P >> 1; s >= 1; s >>= 1) {
+      for (int i = s - 1 + 2 * s * t; i < P; i += 2 * s * kTmThreads) {
+        double v = rhs[i];
+        if (i - s >= 0) v -= ca[i] * rhs[i - s];
+        if (i + s < P) v -= cc[i] * rhs[i + s];
+        rhs[i] = v / cb[i];
+      }
+      __syncthreads();
+    }
+  };
+  auto load_h = [&]() {
+    for (int i = t; i < P; i += kTmThreads) {
+      double a = 0.0, cu = 0.0;
+      if (i < m) {
+        double u[3], ud[3];
+        rod_and_dot(rc, vc, i, u, ud);
+        if (i > 0) {
+          double up[3], upd[3];
+          rod_and_dot(rc, vc, i - 1, up, upd);
+          a = -(up[0] * u[0] + up[1] * u[1] + up[2] * u[2]);
+        }
+        if (i + 1 < m) {
+          double un[3], und[3];
+          rod_and_dot(rc, vc, i + 1, un, und);
+          cu = -(u[0] * un[0] + u[1] * un[1] + u[2] * un[2]);
+        }
+      }
+      ca[i] = a;
+      cb[i] = (i < m) ? 2.0 : 1.0;
+      cc[i] = cu;
+    }
+    __syncthreads();
+  };
+  solve(x1);
+  // rhs of the second solve: c'_k - (H' x)_k
+  for (int i = t; i < P; i += kTmThreads) {
+    double rhs = 0.0;
+    if (i < m) {
+      double u[3], ud[3];
+      rod_and_dot(rc, vc, i, u, ud);
+      const double dy[3] = {yc[3 * i + 3] - yc[3 * i], yc[3 * i + 4] - yc[3 * i + 1], yc[3 * i + 5] - yc[3 * i + 2]};
+      const double dyd[3] = {ydc[3 * i + 3] - ydc[3 * i], ydc[3 * i + 4] - ydc[3 * i + 1],
+                             ydc[3 * i + 5] - ydc[3 * i + 2]};
+      rhs = ud[0] * dy[0] + ud[1] * dy[1] + ud[2] * dy[2] + u[0] * dyd[0] + u[1] * dyd[1] + u[2] * dyd[2];
+      if (i > 0) {
+        double up[3], upd[3];
+        rod_and_dot(rc, vc, i - 1, up, upd);
+        const double hd = -(upd[0] * u[0] + upd[1] * u[1] + upd[2] * u[2] + up[0] * ud[0] + up[1] * ud[1] +
+                            up[2] * ud[2]);
+        rhs -= hd * x1[i - 1];
+      }
+      if (i + 1 < m) {
+        double un[3], und[3];
+        rod_and_dot(rc, vc, i + 1, un, und);
+        const double hd = -(ud[0] * un[0] + ud[1] * un[1] + ud[2] * un[2] + u[0] * und[0] + u[1] * und[1] +
+                            u[2] * und[2]);
+        rhs -= hd * x1[i + 1];
+      }
+    }
+    x2[i] = rhs;
+  }
+  __syncthreads();
+  load_h();
+  solve(x2);
+  // r_m' = r' + (P y)' / 2
+  for (int i = t; i < N; i += kTmThreads) {
+    double p[3] = {ydc[3 * i], ydc[3 * i + 1], ydc[3 * i + 2]};
+    if (i < m) {
+      double u[3], ud[3];
+      rod_and_dot(rc, vc, i, u, ud);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) p[q] += x2[i] * u[q] + x1[i] * ud[q];
+    }
+    if (i > 0) {
+      double up[3], upd[3];
+      rod_and_dot(rc, vc, i - 1, up, upd);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) p[q] -= x2[i - 1] * up[q] + x1[i - 1] * upd[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[3 * i + q] = vc[3 * i + q] + 0.5 * p[q];
+  }
+}
+
+cudaError_t launch_tangent_midpoint_dot(const double* r, const double* rdot, const double* y, const double* ydot,
+                                        const ChainDesc* cd, int n_chains, const int* status, double* rmdot,
+                                        cudaStream_t s) {
+  k_tangent_midpoint_dot<<<n_chains, kTmThreads, 5 * kTmMaxP * sizeof(double), s>>>(r, rdot, y, ydot, cd, status,
+                                                                                    rmdot);
+  return cudaGetLastError();
+}
+
+cudaError_t tangent_configure() {
+  return cudaFuncSetAttribute(k_tangent_midpoint_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(5 * kTmMaxP * sizeof(double)));
+}
+
 // ------------------------------------------------------------ launchers
 cudaError_t launch_assemble_dot(const double* r, const double* rdot, const ChainDesc* cd, int n_chains,
                                 int max_N, double* Md, double hstar, double a, double hdot,
@@ -368,12 +592,33 @@ cudaError_t launch_gemv_dense(const double* A, const ChainDesc* cd, int n_chains
   return cudaGetLastError();
 }
 
-cudaError_t launch_tangent_predictor(const double* r, const double* rdot, const double* ydot,
-                                     const double* uhat, const double* T, const ChainDesc* cd,
+cudaError_t launch_tangent_predictor(const double* r, const double* rdot, const double* rq, const double* rqdot,
+                                     const double* ydot, const double* uhat, const double* T, const ChainDesc* cd,
                                      int n_chains, int max_N, Phys ph, const double* kappa_dot,
                                      double* rsdot, double* G, cudaStream_t s) {
-  k_tangent_predictor<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, rdot, ydot, uhat, T, cd,
-                                                                            ph, kappa_dot, rsdot, G);
+  k_tangent_predictor<<<dim3(ceil_div(max_N, 128), n_chains), 128, 0, s>>>(r, rdot, rq, rqdot, ydot, uhat, T,
+                                                                            cd, ph, kappa_dot, rsdot, G);
+  return cudaGetLastError();
+}
+
+__global__ void k_vec_add(const ChainDesc* __restrict__ cd, const double* __restrict__ a,
+                          const double* __restrict__ b, double* __restrict__ out) {
+  const ChainDesc d = cd[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n) return;
+  const long long o = 3 * d.boff + e;
+  out[o] = a[o] + b[o];
+}
+
+cudaError_t launch_vec_add(const ChainDesc* cd, int n_chains, int max_n, const double* a, const double* b,
+                           double* out, cudaStream_t s) {
+  k_vec_add<<<dim3(ceil_div(max_n, 256), n_chains), 256, 0, s>>>(cd, a, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_upper_matvec(const double* X, const ChainDesc* cd, int n_chains, int max_n,
+                                    const double* xi, double* v, cudaStream_t s) {
+  k_phi_upper_matvec<<<dim3(ceil_div(max_n, 8), n_chains), 256, 0, s>>>(X, cd, xi, v);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 """Pathwise gradients of the mean chain stretch with respect to Wi and h*
-(bd_adjoint, forward-mode tangents of the FP64 step) against central finite
-differences (step 1e-5) of the GPU path and of the FP64 CPU oracle."""
+(bd_adjoint, forward-mode tangents of the FP64 step, midpoint and Euler
+rigid-rod steps) against central finite differences (step 1e-5) of the GPU
+path and of the FP64 CPU oracle."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 NC = np.array([12, 20, 7], np.int32)
 STEPS, DT, WI, HS, FD = 15, 1e-3, 5.0, 0.25, 1e-5
-SCHEME = 1  # the Euler rigid-rod step (the tangents follow that step map)
+SCHEMES = [0, 1]  # midpoint and Euler rigid-rod steps
 
 
 @pytest.fixture(scope="module")
@@ -38,8 +39,8 @@ def stretch_and_grad(r, Nc):
     return J / len(Nc), g / len(Nc)
 
 
-def gpu_run(bd, r0, noise, Wi, hs):
-    ctx = bd.Context(NC, h_star=hs, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=Wi, scheme=SCHEME)
+def gpu_run(bd, r0, noise, Wi, hs, scheme, Nc=NC, dt=DT):
+    ctx = bd.Context(Nc, h_star=hs, dt=dt, flow=bd.FLOW_UNIAXIAL, Wi=Wi, scheme=scheme)
     ctx.set_state(torch.from_numpy(r0).cuda())
     ctx.step(torch.from_numpy(noise).cuda())
     r = ctx.get_state().cpu().numpy()
@@ -49,26 +50,27 @@ def gpu_run(bd, r0, noise, Wi, hs):
     return r
 
 
-def oracle_run(r0, noise, Wi, hs):
-    p = orc.make_params(hstar=hs, dt=DT, flow=orc.FLOW_UNIAXIAL, Wi=Wi, scheme=SCHEME)
-    r, _, st, _, _ = orc.run(p, NC, r0, noise)
+def oracle_run(r0, noise, Wi, hs, scheme, Nc=NC, dt=DT):
+    p = orc.make_params(hstar=hs, dt=dt, flow=orc.FLOW_UNIAXIAL, Wi=Wi, scheme=scheme)
+    r, _, st, _, _ = orc.run(p, Nc, r0, noise)
     assert (st == 0).all()
     return r
 
 
-def test_adjoint_matches_finite_differences(bd):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_adjoint_matches_finite_differences(bd, scheme):
     r0 = inputs.random_walk(NC, 501)
     noise = inputs.gaussian_noise(STEPS, int(NC.sum()), 502)
-    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=SCHEME)
-    r_fin = gpu_run(bd, r0, noise, WI, HS)
+    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=scheme)
+    r_fin = gpu_run(bd, r0, noise, WI, HS, scheme)
     J0, dJdr = stretch_and_grad(r_fin, NC)
     gw, gh = ctx.adjoint(torch.from_numpy(r0).cuda(), torch.from_numpy(noise).cuda(),
                          torch.from_numpy(dJdr).cuda())
     # the context ends at the final state of the same path
     np.testing.assert_allclose(ctx.get_state().cpu().numpy(), r_fin, rtol=0, atol=1e-12)
     ctx.close()
-    Jg = lambda w, h: stretch_and_grad(gpu_run(bd, r0, noise, w, h), NC)[0]
-    Jo = lambda w, h: stretch_and_grad(oracle_run(r0, noise, w, h), NC)[0]
+    Jg = lambda w, h: stretch_and_grad(gpu_run(bd, r0, noise, w, h, scheme), NC)[0]
+    Jo = lambda w, h: stretch_and_grad(oracle_run(r0, noise, w, h, scheme), NC)[0]
     fd_gpu = ((Jg(WI + FD, HS) - Jg(WI - FD, HS)) / (2 * FD), (Jg(WI, HS + FD) - Jg(WI, HS - FD)) / (2 * FD))
     fd_orc = ((Jo(WI + FD, HS) - Jo(WI - FD, HS)) / (2 * FD), (Jo(WI, HS + FD) - Jo(WI, HS - FD)) / (2 * FD))
     for got, a, b in zip((gw, gh), fd_gpu, fd_orc):
@@ -76,16 +78,17 @@ def test_adjoint_matches_finite_differences(bd):
         assert abs(got - b) <= 1e-6 * abs(b), (got, b)
 
 
-def test_autograd_function(bd):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_autograd_function(bd, scheme):
     r0 = torch.from_numpy(inputs.random_walk(NC, 503)).cuda()
     noise = torch.from_numpy(inputs.gaussian_noise(8, int(NC.sum()), 504)).cuda()
     Wi = torch.tensor(WI, dtype=torch.float64, requires_grad=True)
     hs = torch.tensor(HS, dtype=torch.float64, requires_grad=True)
-    r = bd.binding.simulate(Wi, hs, NC, r0, noise, dt=DT, scheme=SCHEME)
+    r = bd.binding.simulate(Wi, hs, NC, r0, noise, dt=DT, scheme=scheme)
     off = np.concatenate([[0], np.cumsum(NC)])
     J = sum((r[off[c + 1] - 1] - r[off[c]]).norm() / (N - 1) for c, N in enumerate(NC)) / len(NC)
     J.backward()
-    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=SCHEME)
+    ctx = bd.Context(NC, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, scheme=scheme)
     _, dJdr = stretch_and_grad(r.detach().cpu().numpy(), NC)
     gw, gh = ctx.adjoint(r0, noise, torch.from_numpy(dJdr).cuda())
     ctx.close()
@@ -99,3 +102,39 @@ def test_adjoint_rejects_mixed_precision(bd):
     with pytest.raises(bd.BDError):
         ctx.adjoint(r0, noise, torch.zeros_like(r0))
     ctx.close()
+
+
+def test_adjoint_uneven_batch_workload(bd):
+    """The uneven-batch workload: 128 chains with N drawn from U{50..500},
+    uniaxial extension Wi = 5, dt = 1e-4, 50 midpoint steps.  The adjoint
+    gradient of the mean stretch matches central finite differences of the
+    GPU path to 1e-6 relative; on the four shortest chains it also matches
+    central finite differences of the oracle."""
+    Nc = inputs.uneven_lengths(128, 50, 500, 1239)
+    steps, dt, wi = 50, 1e-4, 5.0
+    r0 = inputs.random_walk(Nc, 1240)
+    noise = inputs.gaussian_noise(steps, int(Nc.sum()), 1241)
+    r_fin = gpu_run(bd, r0, noise, wi, HS, 0, Nc, dt)
+    J0, dJdr = stretch_and_grad(r_fin, Nc)
+    ctx = bd.Context(Nc, h_star=HS, dt=dt, flow=bd.FLOW_UNIAXIAL, Wi=wi)
+    gw, gh = ctx.adjoint(torch.from_numpy(r0).cuda(), torch.from_numpy(noise).cuda(),
+                         torch.from_numpy(dJdr).cuda())
+    ctx.close()
+    Jg = lambda w, h: stretch_and_grad(gpu_run(bd, r0, noise, w, h, 0, Nc, dt), Nc)[0]
+    fd = ((Jg(wi + FD, HS) - Jg(wi - FD, HS)) / (2 * FD), (Jg(wi, HS + FD) - Jg(wi, HS - FD)) / (2 * FD))
+    for got, want in zip((gw, gh), fd):
+        assert abs(got - want) <= 1e-6 * abs(want), (got, want)
+    # oracle on the four shortest chains (their own adjoint on the GPU)
+    pick = np.argsort(Nc, kind="stable")[:4]
+    off = np.concatenate([[0], np.cumsum(Nc)])
+    sel = np.concatenate([np.arange(off[c], off[c + 1]) for c in pick])
+    Ns = Nc[pick]
+    r0s, nzs = r0[sel], np.ascontiguousarray(noise[:, sel])
+    _, dJs = stretch_and_grad(gpu_run(bd, r0s, nzs, wi, HS, 0, Ns, dt), Ns)
+    cs = bd.Context(Ns, h_star=HS, dt=dt, flow=bd.FLOW_UNIAXIAL, Wi=wi)
+    gws, ghs = cs.adjoint(torch.from_numpy(r0s).cuda(), torch.from_numpy(nzs).cuda(), torch.from_numpy(dJs).cuda())
+    cs.close()
+    Jo = lambda w, h: stretch_and_grad(oracle_run(r0s, nzs, w, h, 0, Ns, dt), Ns)[0]
+    fdo = ((Jo(wi + FD, HS) - Jo(wi - FD, HS)) / (2 * FD), (Jo(wi, HS + FD) - Jo(wi, HS - FD)) / (2 * FD))
+    for got, want in zip((gws, ghs), fdo):
+        assert abs(got - want) <= 1e-6 * abs(want), (got, want)
