@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--dt", type=float, default=1e-4)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--scheme", default="midpoint", choices=["midpoint", "euler"])
+    ap.add_argument("--panel", type=int, default=0, help="factorisation super-panel width (mixed; 0: default)")
+    ap.add_argument("--groups", type=int, default=0, help="factorisation chain groups (mixed; 0: default)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--once", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated bead counts: time one step per N")
@@ -49,6 +51,8 @@ def main():
     ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec,
                      scheme=bd.SCHEME_MIDPOINT if a.scheme == "midpoint" else bd.SCHEME_EULER)
     ctx.set_state(r0)
+    if prec != bd.FP64 and a.panel > 0:
+        bd.lib().bd_set_factor_config(ctx._h, a.panel, a.groups if a.groups > 0 else 1)
     xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 3, int(Nc.sum()), a.seed + 1)).cuda()
     if a.timeline:
         ctx.step(xi[0:1])

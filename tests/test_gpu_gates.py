@@ -125,14 +125,16 @@ def test_ensemble_stretch_against_fp64(bd):
         assert np.abs(a - b).max() < 1e-3 * np.abs(b).max(), col
 
 
-def test_n4000_one_step_mixed_against_fp64(bd):
-    """(iv) One chain of N = 4000 beads (3N = 12000, 94 tiles of 128) under
-    uniaxial extension Wi = 50, dt = 5e-5: one mixed step against one FP64
-    step on the GPU (oracle-pinned path), elementwise to 1e-3 of the largest
-    displacement; rods hold to 1e-10 on both."""
-    Nc = np.array([4000], np.int32)
+@pytest.mark.parametrize("N", [4000, 4096])
+def test_long_chain_one_step_mixed_against_fp64(bd, N):
+    """(iv) One chain of N = 4000 beads (3N = 12000, 94 tiles of 128) and of
+    the per-chain limit N = 4096 (3N = 12288 fills 96 tiles exactly, 4095 rods
+    fill the tension solve) under uniaxial extension Wi = 50, dt = 5e-5: one
+    mixed step against one FP64 step on the GPU (oracle-pinned path),
+    elementwise to 1e-3 of the largest displacement; rods hold to 1e-10."""
+    Nc = np.array([N], np.int32)
     r0 = inputs.random_walk(Nc, 1241)
-    noise = cuda(inputs.gaussian_noise(1, 4000, 1242))
+    noise = cuda(inputs.gaussian_noise(1, N, 1242))
     out = {}
     for prec in (bd.FP64, bd.MIXED_TF32):
         ctx = bd.Context(Nc, h_star=0.25, dt=5e-5, flow=bd.FLOW_UNIAXIAL, Wi=50.0, precision=prec)
