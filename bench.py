@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 from paper_2208_06559_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "chain-timesteps/s at N=1000 (mixed vs FP64, same GPU); Cholesky % tensor peak"
+# DRAM bytes read by one mixed factorisation per chain of N = 1000 (1624.9 MB for 16 chains;
+# the written tiles stay in L2 during the captured launches): ncu capture of the factorisation
+# of 16 chains with the tuned shape.
+FACTOR_TRAFFIC_PER_CHAIN_N1000 = 1624.9e6 / 16
 UNIT = "chain-timesteps/s"
 
 
@@ -258,7 +262,14 @@ def run_ours(args, rank, world, local_rank):
                           "updates; FP32 diagonal tiles)",
                 "frac_of_tf32_peak": achieved_tf / tf32}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes of one factorisation from ncu (dram__bytes_read.sum + dram__bytes_write.sum over
+    # its launches) on 16 chains of N = 1000 with the tuned shape, scaled to the chains here;
+    # profiles/factorisation_traffic_n1000x16_mixed.md.  Other workloads: not captured.
+    roof["traffic"] = (FACTOR_TRAFFIC_PER_CHAIN_N1000 * len(Nc)
+                       if prec != bd.FP64 and int(Nc.min()) == 1000 == int(Nc.max()) else None)
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = "ncu, 16 chains x N=1000 (panel 16, 4 groups), scaled by chains"
+        roof["algorithmic_bytes_per_launch"] = float(np.sum((np.ceil(n / 128) * 128) ** 2)) * 4.0  # lower triangle read + written
     roof["algorithmic_flops_per_launch"] = chol_flops
     roof["ms_per_launch"] = fms
     others = {"mobility_symv": hbm_roofline(symv_bytes, stage["mobility_symv_ms"], peaks["hbm_gbs"]),
