@@ -106,7 +106,7 @@ typedef enum { BD_SCHEME_MIDPOINT = 0, BD_SCHEME_EULER = 1 } bd_scheme;
 
 typedef struct {
   int n_chains;          /* >= 1 */
-  const int* n_beads;    /* host array [n_chains], each N_c >= 2; uneven allowed */
+  const int* n_beads;    /* host array [n_chains], each 2 <= N_c <= 4096 (BD_FP64) or 8192 (mixed); uneven allowed */
   double h_star;         /* HI parameter h* >= 0 (Eqs. (8)-(9)) */
   double a;              /* bead radius; <= 0 means a = h*; a < h* is rejected */
   double dt;             /* time step > 0 */

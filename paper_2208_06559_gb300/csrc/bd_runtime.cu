@@ -676,11 +676,14 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   if (p->constraint != BD_RIGID && p->constraint != BD_FRAENKEL) return BD_ERR_ARG;
   if (p->constraint == BD_FRAENKEL && !(p->k_spring > 0.0 && p->k_spring < 1e300)) return BD_ERR_ARG;
   if (p->scheme != BD_SCHEME_MIDPOINT && p->scheme != BD_SCHEME_EULER) return BD_ERR_ARG;
-  // limits of the per-chain kernels: the tension solve holds N - 1 <= 4096
-  // unknowns in shared memory; the refinement's triangular solve owns up to
-  // 12 columns per thread of a 1024-thread block (3N <= 12288 after padding)
+  // limits of the per-chain kernels: FP64 path, N <= 4096 (the tension solve
+  // holds N - 1 unknowns in shared memory, the back substitution owns 12
+  // columns per thread); mixed path, N <= 8192 (the super-block tension solve
+  // holds N - 1 unknowns in shared memory, the refinement's triangular solve
+  // spreads 3N <= 24576 columns over a cluster of four CTAs)
+  const int max_beads = (p->precision == BD_FP64) ? 4096 : 8192;
   for (int i = 0; i < p->n_chains; ++i)
-    if (p->n_beads[i] < 2 || p->n_beads[i] > 4096) return BD_ERR_ARG;
+    if (p->n_beads[i] < 2 || p->n_beads[i] > max_beads) return BD_ERR_ARG;
 
   bd_ctx* c = new (std::nothrow) bd_ctx();
   if (!c) return BD_ERR_OOM;

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_newton_residual_g(const double* __restr
 // summed from it.  Failed chains keep their
 // positions; the step index advances as in k_finalize.
 constexpr int kFinThreads = 1024;
-constexpr int kFinPer = 4;  // beads per thread (N <= 4096)
+constexpr int kFinPer = 8;  // beads per thread (N <= 8192)
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize_g(const ChainDesc* __restrict__ cd, Phys ph,
                                                             const double* __restrict__ rpos,
@@ -305,9 +305,9 @@ cudaError_t launch_finalize_g(const ChainDesc* cd, int n_chains, Phys ph, const 
 }
 
 cudaError_t gmode_configure() {
-  // T split for chains of up to 4096 beads: 4096 x (hi, lo) floats
+  // T split for chains of up to 8192 beads: 8192 x (hi, lo) floats
   return cudaFuncSetAttribute(k_gemv_g, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(4096 * 2 * sizeof(float)));
+                              (int)(8192 * 2 * sizeof(float)));
 }
 
 }  // namespace bd

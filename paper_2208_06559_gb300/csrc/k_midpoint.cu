@@ -31,7 +31,9 @@
 namespace bd {
 
 constexpr int kMidThreads = 1024;
-constexpr int kMidMaxP = 4096;  // rods padded to a power of two (N <= 4096)
+constexpr int kMidMaxP = 4096;     // cyclic reduction: rods padded to a power of two <= 4096
+constexpr int kMidMaxRods = 8192;  // serial elimination beyond that (N <= 8192)
+constexpr int kMidSmem = (4 * kMidMaxP > 3 * kMidMaxRods ? 4 * kMidMaxP : 3 * kMidMaxRods) * (int)sizeof(double);
 
 __device__ __forceinline__ void rod_dir(const double* rc, int k, double u[3]) {
   const double q0 = rc[3 * k + 3] - rc[3 * k], q1 = rc[3 * k + 4] - rc[3 * k + 1],
@@ -45,7 +47,9 @@ __device__ __forceinline__ void rod_dir(const double* rc, int k, double u[3]) {
 // One CTA per chain.  (A A^T) x = A y by cyclic reduction over P = 2^L >= m
 // equations (the padding rows are x = 0): the forward levels eliminate the
 // odd-indexed neighbours in place (A A^T is symmetric positive definite, so
-// the elimination needs no pivoting), the backward levels recover x.  Then
+// the elimination needs no pivoting), the backward levels recover x.  Chains
+// of more than 4096 rods, whose four work arrays would not fit in shared
+// memory, take the serial elimination (Thomas) by one thread instead.  Then
 // r_m = r + (y - A^T x) / 2 and u_m.  Chains with a nonzero status keep
 // r_m = r.  y is yscale times `y_in`, or times the step's noise when args is
 // not NULL.
@@ -70,6 +74,59 @@ __global__ void __launch_bounds__(kMidThreads) k_tangent_midpoint(const double* 
   } else {
     int P = 1;
     while (P < m) P <<= 1;
+    if (P > kMidMaxP) {
+      // c_i (super-diagonal, also the next row's sub-diagonal), c'_i, then
+      // d_i -> d'_i -> x_i
+      double* c0 = tm_smem;
+      double* cp = tm_smem + kMidMaxRods;
+      double* dd = tm_smem + 2 * kMidMaxRods;
+      for (int i = t; i < m; i += kMidThreads) {
+        double ui[3];
+        rod_dir(rc, i, ui);
+        double cu = 0.0;
+        if (i + 1 < m) {
+          double un[3];
+          rod_dir(rc, i + 1, un);
+          cu = -(ui[0] * un[0] + ui[1] * un[1] + ui[2] * un[2]);
+        }
+        c0[i] = cu;
+        dd[i] = yscale * (ui[0] * (yc[3 * i + 3] - yc[3 * i]) + ui[1] * (yc[3 * i + 4] - yc[3 * i + 1]) +
+                          ui[2] * (yc[3 * i + 5] - yc[3 * i + 2]));
+      }
+      __syncthreads();
+      if (t == 0) {
+        double cprev = c0[0] / 2.0;
+        cp[0] = cprev;
+        dd[0] = dd[0] / 2.0;
+        for (int i = 1; i < m; ++i) {
+          const double a = c0[i - 1];  // H_{i,i-1} = H_{i-1,i}
+          const double den = 2.0 - a * cprev;
+          cprev = c0[i] / den;
+          cp[i] = cprev;
+          dd[i] = (dd[i] - a * dd[i - 1]) / den;
+        }
+        for (int i = m - 2; i >= 0; --i) dd[i] -= cp[i] * dd[i + 1];
+      }
+      __syncthreads();
+      for (int i = t; i < N; i += kMidThreads) {
+        double p[3] = {yscale * yc[3 * i], yscale * yc[3 * i + 1], yscale * yc[3 * i + 2]};
+        if (i < m) {
+          double ui[3];
+          rod_dir(rc, i, ui);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) p[q] += dd[i] * ui[q];
+        }
+        if (i > 0) {
+          double up[3];
+          rod_dir(rc, i - 1, up);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) p[q] -= dd[i - 1] * up[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rm[3 * i + q] = rc[3 * i + q] + 0.5 * p[q];
+      }
+      __syncthreads();
+    } else {
     double* ca = tm_smem;           // sub-diagonal coefficient
     double* cb = tm_smem + P;       // diagonal
     double* cc = tm_smem + 2 * P;   // super-diagonal
@@ -154,6 +211,7 @@ __global__ void __launch_bounds__(kMidThreads) k_tangent_midpoint(const double* 
       for (int q = 0; q < 3; ++q) rm[3 * i + q] = rc[3 * i + q] + 0.5 * p[q];
     }
     __syncthreads();
+    }
   }
   for (int k = t; k < m; k += kMidThreads) {
     double u[3];
@@ -168,8 +226,7 @@ __global__ void __launch_bounds__(kMidThreads) k_tangent_midpoint(const double* 
 cudaError_t launch_tangent_midpoint(const double* r, const double* y, const StepArgs* args, double yscale,
                                     const ChainDesc* cd, int n_chains, const int* status, double* rmid,
                                     double* umid, cudaStream_t s) {
-  k_tangent_midpoint<<<n_chains, kMidThreads, 4 * kMidMaxP * sizeof(double), s>>>(r, y, args, yscale, cd, status,
-                                                                                  rmid, umid);
+  k_tangent_midpoint<<<n_chains, kMidThreads, kMidSmem, s>>>(r, y, args, yscale, cd, status, rmid, umid);
   return cudaGetLastError();
 }
 
@@ -335,8 +392,7 @@ cudaError_t launch_mob_delta_f32(const double* r, const double* rmid, const doub
 }
 
 cudaError_t midpoint_configure() {
-  return cudaFuncSetAttribute(k_tangent_midpoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(4 * kMidMaxP * sizeof(double)));
+  return cudaFuncSetAttribute(k_tangent_midpoint, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem);
 }
 
 }  // namespace bd

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_trmv_f32(const float* __restrict__ M,
 // eight partial sums per output) every owned column a < 128 b gets
 // sum_{rho in b} Lt[rho][a] z_rho: each row of Lt is read once, coalesced.
 constexpr int kTrsvThreads = 1024;
-constexpr int kTrsvMaxCols = 12;  // np <= 12288 (N <= 4096)
+constexpr int kTrsvMaxCols = 24;  // np <= 24576 (N <= 8192) with 4-CTA clusters
 constexpr int kTrsvW = kMixedTile * kMixedTile;
 constexpr int kTrsvSmem = (2 * kTrsvW + 2 * 8 * kMixedTile) * 4;  // W_b double buffer, partials
 
@@ -129,17 +129,18 @@ __device__ __forceinline__ void trsv_cp16(float* smem, const float* gmem) {
                : "memory");
 }
 
-// The solve is split over a cluster of two CTAs per chain: CTA `rank` owns
-// the columns of the 128-wide blocks B with B % 2 == rank (local column
-// l = t + 1024 q -> block 2 (l / 128) + rank).  For block b the owner
-// publishes its 128 accumulated sums through distributed shared memory,
-// both CTAs form z_b (the same arithmetic, so identical copies), and each
-// adds block b's contributions to the columns it owns.  W_{b-1} is copied
-// (cp.async) into the other half of a double buffer while block b is
-// processed.  Rank 0 writes z.
-constexpr int kTrsvColsCl = 6;  // owned columns per thread: np <= 12288
+// The solve is split over a cluster of CL CTAs per chain (CL = 2 for
+// np <= 12288, 4 up to 24576): CTA `rank` owns the columns of the 128-wide
+// blocks B with B % CL == rank (local column l = t + 1024 q -> block
+// CL (l / 128) + rank).  For block b the owner publishes its 128 accumulated
+// sums through distributed shared memory, every CTA forms z_b (the same
+// arithmetic, so identical copies), and each adds block b's contributions to
+// the columns it owns.  W_{b-1} is copied (cp.async) into the other half of a
+// double buffer while block b is processed.  Rank 0 writes z.
+constexpr int kTrsvColsCl = 6;  // owned columns per thread: np <= 6144 CL
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kTrsvThreads)
     k_trsv_t_f32c(const float* __restrict__ M, const float* __restrict__ Winv, const ChainDesc* __restrict__ cd,
                   const double* __restrict__ x_in, const StepArgs* __restrict__ args, double* __restrict__ z) {
   namespace cg = cooperative_groups;
@@ -151,7 +152,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
   float* pl = ph + 8 * kMixedTile;           // [8][128] partial lo
   __shared__ float pub_h[2][128], pub_l[2][128];  // published sums of an owned block (by parity)
   __shared__ float zh[128], zl[128], sh[128], sl[128];
-  const ChainDesc d = cd[blockIdx.x >> 1];
+  const ChainDesc d = cd[blockIdx.x / CL];
   const int T = d.np / kMixedTile;
   const double* x = args ? args->noise + (long long)args->step * args->stride : x_in;
   x += 3 * d.boff;
@@ -163,7 +164,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
   for (int q = 0; q < kTrsvColsCl; ++q) acc[q] = DFa{0.f, 0.f};
   auto col_of = [&](int q) {  // global column of owned slot q (may be >= np)
     const int l = t + kTrsvThreads * q;
-    return kMixedTile * (2 * (l >> 7) + rank) + (l & 127);
+    return kMixedTile * (CL * (l >> 7) + rank) + (l & 127);
   };
   auto stage_w = [&](int b, float* dst) {  // W_bb -> dst, 16 KB per quarter, one group
     const float* Wg = Winv + ((long long)d.wrow + kMixedTile * b) * kMixedTile;
@@ -177,7 +178,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
     const int c0 = 128 * b;
     float* Ws = Wbuf + par * kTrsvW;
     if (b > 0) stage_w(b - 1, Wbuf + (par ^ 1) * kTrsvW);
-    if ((b & 1) == rank) {  // publish the sums of block b's columns
+    if ((b % CL) == rank) {  // publish the sums of block b's columns
 #pragma unroll
       for (int q = 0; q < kTrsvColsCl; ++q) {
         const int a = col_of(q);
@@ -189,7 +190,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
     }
     cl.sync();
     if (t < 128) {
-      const int owner = b & 1;
+      const int owner = b % CL;
       const float* qh = owner == rank ? pub_h[par] : cl.map_shared_rank(&pub_h[par][0], owner);
       const float* ql = owner == rank ? pub_l[par] : cl.map_shared_rank(&pub_l[par][0], owner);
       const int a = c0 + t;
@@ -257,7 +258,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTrsvThreads)
     }
     __syncthreads();
   }
-  cl.sync();  // no CTA leaves while its partner may still read its shared memory
+  cl.sync();  // no CTA leaves while a partner may still read its shared memory
 }
 
 // y = scale / 2 (y1 + w)   (scale already applied to y1 when y1 was formed
@@ -285,7 +286,10 @@ cudaError_t launch_brownian_f32_begin(const float* M, const float* Winv, const C
   cudaError_t e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
   if (e != cudaSuccess) return e;
-  k_trsv_t_f32c<<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
+  if (max_np <= 2 * 6 * kTrsvThreads)
+    k_trsv_t_f32c<2><<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
+  else
+    k_trsv_t_f32c<4><<<4 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
   if (refine)
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
   else
@@ -321,7 +325,9 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
 }
 
 cudaError_t refine_configure() {
-  return cudaFuncSetAttribute(k_trsv_t_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_trsv_t_f32c<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_trsv_t_f32c<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  return e;
 }
 
 }  // namespace bd

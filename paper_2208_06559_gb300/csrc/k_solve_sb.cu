@@ -30,7 +30,7 @@ constexpr int kTP = 65;              // shared-memory pitch of a 64 x 64 tile
 constexpr int kSbInvThreads = 256;
 constexpr int kSbInvSmem = 3 * 64 * kTP * (int)sizeof(float);
 constexpr int kSbThreads = 1024;
-constexpr int kSbMaxM = 4096;        // rods per chain (N <= 4096 beads)
+constexpr int kSbMaxM = 8192;        // rods per chain (N <= 8192 beads)
 
 // One CTA per (chain, super-block S, column block j): V_S's column block j,
 // rows j .. end of the super-block, top-down.  Each finished block V_ij goes

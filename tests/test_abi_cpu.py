@@ -60,7 +60,8 @@ def test_strerror_and_defaults(lib):
     lambda p, nb: setattr(p, "precision", 2),   # BF16 operands: no such factorisation is built
     lambda p, nb: setattr(p, "scheme", 2),
     lambda p, nb: nb.__setitem__(0, 1),   # a chain needs >= 2 beads
-    lambda p, nb: nb.__setitem__(1, 4097),  # past the per-chain kernel limit of 4096 beads
+    lambda p, nb: nb.__setitem__(1, 4097),  # past the FP64 path's per-chain limit of 4096 beads
+    lambda p, nb: (setattr(p, "precision", 1), nb.__setitem__(1, 8193)),  # past the mixed path's 8192
     lambda p, nb: setattr(p, "dt", float("nan")),
     lambda p, nb: setattr(p, "h_star", float("nan")),
     lambda p, nb: setattr(p, "dt", float("inf")),

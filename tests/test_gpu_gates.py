@@ -148,3 +148,60 @@ def test_long_chain_one_step_mixed_against_fp64(bd, N):
     d64 = out[bd.FP64] - r0
     err = np.abs(out[bd.MIXED_TF32] - out[bd.FP64]).max() / np.abs(d64).max()
     assert err < 1e-3, err
+
+
+@pytest.mark.parametrize("N", [6000, 8192])
+def test_chains_beyond_4096_beads(bd, N):
+    """The mixed path takes chains of up to 8192 beads (3N = 24576, 192 tiles;
+    the refinement's triangular solve on a cluster of four CTAs, the midpoint
+    projection by serial elimination past 4095 rods).  One chain: the
+    midpoint r_m matches r + P y / 2 computed here with a banded solve of
+    (A A^T) x = A y from s Lt xi of the library's own factor (to the FP32
+    summation error of its product, 1e-5 of the largest displacement), and two steps of uniaxial extension hold every rod to
+    1e-10.  At N = 6000 the refined Brownian displacement also agrees with
+    s L xi of an FP64 LAPACK factor of the oracle's D to the factor's
+    first-order error."""
+    sp = pytest.importorskip("scipy.linalg")
+    Nc = np.array([N], np.int32)
+    r0 = inputs.random_walk(Nc, 1243)
+    xi = inputs.gaussian_noise(2, N, 1244)
+    dt = 5e-5
+    s = np.sqrt(2 * dt)
+    ctx = bd.Context(Nc, h_star=0.25, dt=dt, flow=bd.FLOW_UNIAXIAL, Wi=50.0, precision=bd.MIXED_TF32)
+    ctx.set_state(cuda(r0))
+    ctx.assemble()
+    ctx.factor()
+    st, _ = ctx.chain_status()
+    assert (st == 0).all(), st
+    assert ctx.factor_residual(0) < 1e-3
+    rm, _ = ctx.midpoint(cuda(xi[0]))
+    rm = rm.cpu().numpy()
+    L = ctx.read_matrix(0, 1)
+    yB = (s * (L @ xi[0].ravel())).reshape(N, 3)   # the raw displacement that places r_m
+    Q = np.diff(r0, axis=0)
+    u = Q / np.linalg.norm(Q, axis=1)[:, None]
+    c = (u * (yB[1:] - yB[:-1])).sum(1)
+    off = -(u[:-1] * u[1:]).sum(1)
+    ab = np.zeros((3, N - 1))
+    ab[0, 1:] = off
+    ab[1, :] = 2.0
+    ab[2, :-1] = off
+    x = sp.solve_banded((1, 1), ab, c)
+    Py = yB.copy()
+    Py[:-1] += x[:, None] * u
+    Py[1:] -= x[:, None] * u
+    np.testing.assert_allclose(rm, r0 + 0.5 * Py, rtol=0, atol=1e-5 * np.abs(yB).max())
+    if N == 6000:
+        D = orc.assemble(r0, 0.25, 0.25)
+        Lx = np.linalg.cholesky(D)
+        del D
+        y = ctx.brownian(cuda(xi[0])).cpu().numpy().ravel()
+        y64 = s * (Lx @ xi[0].ravel())
+        assert np.abs(y - y64).max() / np.abs(y64).max() < 1e-2
+    del L
+    ctx.set_state(cuda(r0))
+    ctx.step(cuda(xi))
+    obs, st = ctx.observables()
+    assert (st == 0).all(), st
+    assert obs[:, bd.OBS_MAXDEV].max().item() < 1e-10
+    ctx.close()
