@@ -146,8 +146,11 @@ int bd_get_state(bd_ctx* ctx, double* r_dev, void* stream);
 /* Advance every chain by n_steps >= 1 time steps.  noise: [n_steps][sum N][3]
  * FP64 i.i.d. N(0,1) numbers, device or host memory, owned by the caller and
  * read during the call's stream work (host memory is copied before return of
- * the staged copies).  Asynchronous; returns BD_OK unless the arguments or a
- * CUDA call fail.  Errors: BD_ERR_ARG, BD_ERR_STATE, BD_ERR_CUDA. */
+ * the staged copies).  All n_steps run in one launch of the context's CUDA
+ * graph, whose outer WHILE node loops over the steps on the device (the
+ * first call captures and instantiates the graph).  Asynchronous; returns
+ * BD_OK unless the arguments or a CUDA call fail.  Errors: BD_ERR_ARG,
+ * BD_ERR_STATE, BD_ERR_CUDA. */
 int bd_step(bd_ctx* ctx, int n_steps, const double* noise, void* stream);
 
 /* Per-chain observables [n_chains][BD_OBS_STRIDE] FP64 into obs (device or
@@ -176,8 +179,8 @@ int bd_chain_status(bd_ctx* ctx, int* status_host, int* newton_host, void* strea
 int bd_profile_step(bd_ctx* ctx, const double* noise, int newton_iters, double* ms_out);
 
 /* Number of kernel launches executed by bd_step on this context since its
- * creation (the captured step graph's kernels times the steps, plus the
- * kernels of every executed tension-solve iteration).  Synchronises the
+ * creation (the kernels of one step of the captured graph times the steps,
+ * plus the kernels of every executed tension-solve iteration).  Synchronises the
  * stream. */
 int bd_kernel_launches(bd_ctx* ctx, unsigned long long* out, void* stream);
 

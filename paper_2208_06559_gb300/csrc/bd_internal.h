@@ -54,8 +54,9 @@ struct Phys {
 struct StepArgs {
   const double* noise;  // [n_steps][sum N][3]
   long long stride;     // sum N * 3
-  int step;             // replay index within the current bd_step call
+  int step;             // step index within the current bd_step call
   int loops_in_step;    // tension-solve loop iterations in the current step
+  int n_steps;          // steps of the current bd_step call
 };
 
 constexpr int kSimtTile = 32;     // SIMT Cholesky tile (FP64, FP32) and K tile
@@ -155,8 +156,10 @@ cudaError_t launch_finalize(const ChainDesc* cd, int n_chains, long long total_b
                             StepArgs* args, cudaStream_t s);
 cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chains,
                                const int* iters, const double* T, double* obs, cudaStream_t s);
-cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
+cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride, int n_steps,
                             cudaStream_t s);
+// Ends one step of the step graph's WHILE loop: continue while steps remain.
+cudaError_t launch_step_loop(const StepArgs* args, cudaGraphConditionalHandle h, cudaStream_t s);
 // FP32 Cholesky of the rod-coupling matrix with 64-wide tiles (k_chol_k64.cu);
 // mp must be a multiple of 64; the 64 x 64 diagonal-tile inverses go to Kinv.
 cudaError_t k64_configure();

@@ -418,53 +418,45 @@ int enqueue_step_fraenkel(bd_ctx* c, cudaStream_t s) {
   return BD_OK;
 }
 
-int build_step_graph(bd_ctx* c) {
-  if (c->exec) return BD_OK;
-  if (c->fraenkel) {
-    cudaStream_t s = c->cs;
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_step_fraenkel(c, s);
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamEndCapture(s, &g));
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    set_graph_priorities(c, g);
-    c->graph = g;
-    c->graph_kernels = count_kernel_nodes(g);
-    c->body_kernels = 0;
-    CK(cudaGraphInstantiate(&c->exec, g, cudaGraphInstantiateFlagUseNodePriority));
-    return BD_OK;
-  }
+// Captures one step into `step` (the body of the graph's outer WHILE node):
+// the pre-solve stages, the first graph_unroll tension iterations as plain
+// nodes (chains that have converged skip them on the device), an inner WHILE
+// node for the rest, the commit, and the outer loop's condition.  *inner
+// receives the inner WHILE node's body (null in Fraenkel mode).
+static int capture_step(bd_ctx* c, cudaGraph_t step, cudaGraphConditionalHandle hs, cudaGraph_t* inner) {
+  *inner = nullptr;
   cudaStream_t s = c->cs;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  CK(cudaStreamBeginCaptureToGraph(s, step, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  auto end_capture = [&](int rc) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);  // `step` is owned by its WHILE node
+    return rc ? rc : (e == cudaSuccess ? BD_OK : BD_ERR_CUDA);
+  };
+  if (c->fraenkel) {
+    int rc = enqueue_step_fraenkel(c, s);
+    if (rc == BD_OK && launch_step_loop(c->args, hs, s) != cudaSuccess) rc = BD_ERR_CUDA;
+    return end_capture(rc);
+  }
   int rc = enqueue_pre_newton(c, s);
-  // the first graph_unroll tension iterations are plain nodes (chains that
-  // have converged skip them on the device); the WHILE node takes the rest
   for (int i = 0; rc == BD_OK && i < c->graph_unroll; ++i) rc = enqueue_newton_iter(c, s, i == 0);
   if (rc == BD_OK && c->graph_unroll == 0 && c->mixed && cudaStreamWaitEvent(s, c->aev[1], 0) != cudaSuccess)
     rc = BD_ERR_CUDA;
   c->while_cap = c->ph.max_newton + 3 - c->graph_unroll;
   if (c->while_cap < 1) c->while_cap = 1;
-  cudaGraph_t g = nullptr;
-  if (rc) {
-    cudaStreamEndCapture(s, &g);
-    if (g) cudaGraphDestroy(g);
-    return rc;
-  }
+  if (rc) return end_capture(rc);
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   cudaGraph_t cg = nullptr;
-  CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
   cudaGraphConditionalHandle h;
-  CK(cudaGraphConditionalHandleCreate(&h, cg, c->graph_unroll > 0 ? 0 : 1, cudaGraphCondAssignDefault));
-  if (c->graph_unroll > 0) {
-    // enter the loop only if a chain is still iterating
-    CK(launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->while_cap, false, s));
-    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
-  }
+  // The inner loop's condition is set by a kernel in every step (enter only
+  // if a chain is still iterating), not left to the handle's default.
+  if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+      launch_newton_any_active(c->state, c->n_chains, h, c->loops, c->args, c->while_cap, false, s) !=
+          cudaSuccess ||
+      cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess)
+    return end_capture(BD_ERR_CUDA);
   // cudaGraphNodeParams holds a union without a default constructor
   alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
   memset(cp_buf, 0, sizeof(cp_buf));
@@ -474,31 +466,60 @@ int build_step_graph(bd_ctx* c) {
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
-  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  if (cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+      cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+          cudaSuccess)
+    return end_capture(BD_ERR_CUDA);
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK(cudaStreamBeginCaptureToGraph(c->cs2, body, nullptr, nullptr, 0,
-                                   cudaStreamCaptureModeThreadLocal));
+  if (cudaStreamBeginCaptureToGraph(c->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return end_capture(BD_ERR_CUDA);
   rc = enqueue_newton_body(c, h, c->cs2);
   cudaGraph_t body_out = nullptr;
-  CK(cudaStreamEndCapture(c->cs2, &body_out));
+  if (cudaStreamEndCapture(c->cs2, &body_out) != cudaSuccess && rc == BD_OK) rc = BD_ERR_CUDA;
+  if (rc == BD_OK) rc = enqueue_finalize(c, s);
+  if (rc == BD_OK && launch_step_loop(c->args, hs, s) != cudaSuccess) rc = BD_ERR_CUDA;
+  *inner = body;
+  return end_capture(rc);
+}
+
+// The step graph: one WHILE node whose body is one step (capture_step); the
+// commit advances the step index and the body's last kernel continues the
+// loop while steps of the bd_step call remain, so one launch of the graph
+// advances every chain of the batch, however uneven, by all the steps of the
+// call.  The condition's default is 1: every launch runs at least one step.
+int build_step_graph(bd_ctx* c) {
+  if (c->exec) return BD_OK;
+  cudaGraph_t top = nullptr;
+  CK(cudaGraphCreate(&top, 0));
+  cudaGraphConditionalHandle hs;
+  alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
+  memset(cp_buf, 0, sizeof(cp_buf));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_buf);
+  cudaGraphNode_t node;
+  cudaGraph_t inner = nullptr;
+  int rc = BD_OK;
+  if (cudaGraphConditionalHandleCreate(&hs, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    rc = BD_ERR_CUDA;
+  } else {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hs;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &cp) != cudaSuccess) rc = BD_ERR_CUDA;
+  }
+  cudaGraph_t step = rc == BD_OK ? cp.conditional.phGraph_out[0] : nullptr;
+  if (rc == BD_OK) rc = capture_step(c, step, hs, &inner);
   if (rc) {
-    cudaStreamEndCapture(s, &g);
-    if (g) cudaGraphDestroy(g);
+    cudaGraphDestroy(top);
     return rc;
   }
-  if ((rc = enqueue_finalize(c, s))) {
-    cudaStreamEndCapture(s, &g);
-    if (g) cudaGraphDestroy(g);
-    return rc;
-  }
-  CK(cudaStreamEndCapture(s, &g));
-  set_graph_priorities(c, g);
-  set_graph_priorities(c, body);
-  c->graph = g;
-  c->graph_kernels = count_kernel_nodes(g);
-  c->body_kernels = count_kernel_nodes(body);
-  CK(cudaGraphInstantiate(&c->exec, g, cudaGraphInstantiateFlagUseNodePriority));
+  set_graph_priorities(c, step);
+  if (inner) set_graph_priorities(c, inner);
+  c->graph = top;
+  c->graph_kernels = count_kernel_nodes(step);  // per step
+  c->body_kernels = inner ? count_kernel_nodes(inner) : 0;
+  CK(cudaGraphInstantiate(&c->exec, top, cudaGraphInstantiateFlagUseNodePriority));
   return BD_OK;
 }
 
@@ -919,7 +940,7 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
                        cudaMemcpyHostToDevice, s));
     nz = c->stage;
   }
-  CK(launch_set_args(c->args, nz, stride, s));
+  CK(launch_set_args(c->args, nz, stride, n_steps, s));
   // The steps run on the context's highest-priority stream, ordered after the
   // caller's work on `stream` and before the caller's later work on it (a
   // default-priority caller stream would share the lowest priority with the
@@ -931,7 +952,7 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
     for (int i = 0; i < n_steps; ++i)
       if ((rc = enqueue_step_direct(c, cs))) return rc;
   } else {
-    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->exec, cs));
+    CK(cudaGraphLaunch(c->exec, cs));  // all n_steps steps in one launch
     c->steps_launched += (unsigned long long)n_steps;
   }
   CK(cudaEventRecord(c->aev[5], cs));
@@ -957,7 +978,7 @@ int bd_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms
     c->prof = ev;
     c->direct_iters = newton_iters > 0 ? newton_iters : c->ph.max_newton + 2;
     const long long stride = c->total_beads * 3;
-    if (launch_set_args(c->args, noise, stride, s) != cudaSuccess) rc = BD_ERR_CUDA;
+    if (launch_set_args(c->args, noise, stride, 1, s) != cudaSuccess) rc = BD_ERR_CUDA;
     if (rc == BD_OK) rc = enqueue_step_direct(c, s);
     if (rc == BD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BD_ERR_CUDA;
     c->prof = nullptr;

@@ -449,16 +449,28 @@ cudaError_t launch_observables(const double* r, const ChainDesc* cd, int n_chain
   return cudaGetLastError();
 }
 
-__global__ void k_set_args(StepArgs* args, const double* noise, long long stride) {
+__global__ void k_set_args(StepArgs* args, const double* noise, long long stride, int n_steps) {
   args->noise = noise;
   args->stride = stride;
   args->step = 0;
   args->loops_in_step = 0;
+  args->n_steps = n_steps;
 }
 
-cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride,
+cudaError_t launch_set_args(StepArgs* args, const double* noise, long long stride, int n_steps,
                             cudaStream_t s) {
-  k_set_args<<<1, 1, 0, s>>>(args, noise, stride);
+  k_set_args<<<1, 1, 0, s>>>(args, noise, stride, n_steps);
+  return cudaGetLastError();
+}
+
+// The step graph's outer WHILE condition, after the step's commit has
+// advanced args->step.
+__global__ void k_step_loop(const StepArgs* args, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, args->step < args->n_steps ? 1u : 0u);
+}
+
+cudaError_t launch_step_loop(const StepArgs* args, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_step_loop<<<1, 1, 0, s>>>(args, h);
   return cudaGetLastError();
 }
 

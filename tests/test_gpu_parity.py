@@ -229,6 +229,44 @@ def test_two_calls_equal_one_call(bd):
     b.close()
 
 
+@pytest.mark.parametrize("precision,unroll", [(0, None), (0, "0"), (1, None), (1, "0")])
+def test_one_graph_launch_runs_every_step(bd, monkeypatch, precision, unroll):
+    """bd_step advances every chain of an uneven batch by all n steps in one
+    launch of the step graph (an outer WHILE node loops over the steps on the
+    device): five steps in one call equal five one-step calls bit for bit,
+    also with no tension iteration captured ahead of the inner WHILE node
+    (its condition is set anew in every step), and both runs count the same
+    kernels.  The five-step run also matches the oracle."""
+    if unroll is not None:
+        monkeypatch.setenv("BD_GRAPH_UNROLL", unroll)
+    Nc = np.array([40, 9, 61], np.int32)
+    r0 = inputs.random_walk(Nc, 31)
+    noise = inputs.gaussian_noise(5, int(Nc.sum()), 32)
+    kw = dict(h_star=0.25, dt=1e-3, flow=bd.FLOW_SHEAR, Wi=5.0, precision=precision)
+    a = bd.Context(Nc, **kw)
+    a.set_state(cuda(r0))
+    a.step(cuda(noise))
+    b = bd.Context(Nc, **kw)
+    b.set_state(cuda(r0))
+    for k in range(5):
+        b.step(cuda(noise[k:k + 1]))
+    ra, rb = a.get_state().cpu().numpy(), b.get_state().cpu().numpy()
+    np.testing.assert_array_equal(ra, rb)
+    assert a.kernel_launches() == b.kernel_launches() > 0
+    for ctx in (a, b):
+        st, _ = ctx.chain_status()
+        assert (st == 0).all(), st
+        ctx.close()
+    p = orc.make_params(hstar=0.25, dt=1e-3, flow=orc.FLOW_SHEAR, Wi=5.0)
+    rr, _, st_ref, _, _ = orc.run(p, Nc, r0, noise)
+    assert (st_ref == 0).all()
+    if precision == 0:
+        assert np.abs(ra - rr).max() <= 1e-10 * np.abs(rr).max()
+    else:  # displacements, to the factor's first-order error (as in the accuracy gates)
+        d, dr = ra - r0, rr - r0
+        assert np.abs(d - dr).max() <= 1e-3 * np.abs(dr).max(), np.abs(d - dr).max()
+
+
 # ------------------------------------------------------------- failures
 def test_not_pd_chain_is_frozen_and_others_advance(bd):
     """Two coincident beads with a = h* make D singular: that chain reports
