@@ -163,8 +163,8 @@ cudaError_t launch_step_loop(const StepArgs* args, cudaGraphConditionalHandle h,
 // FP32 Cholesky of the rod-coupling matrix with 64-wide tiles (k_chol_k64.cu);
 // mp must be a multiple of 64; the 64 x 64 diagonal-tile inverses go to Kinv.
 cudaError_t k64_configure();
-cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
-                            int* status, cudaStream_t s);
+cudaError_t launch_chol_k64(float* K, float* Kinv, const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains,
+                            int max_tiles, int* status, cudaStream_t s);
 
 // Opt-in shared-memory sizes of the matvec kernels (once per device).
 cudaError_t matvec_configure();
@@ -228,6 +228,13 @@ cudaError_t midpoint_configure();
 bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, const ChainDesc* h_cd,
                   int n_chains);
 cudaError_t tc_configure();
+// TMA maps of every chain's FP32 K, for the tensor-core update of K's factorisation.
+bool make_k_maps(CUtensorMap* host_maps, float* K, const ChainDesc* h_cd, int n_chains);
+// K_ij -= L_ik L_jk^T after K's 64-wide block column k, FP32-accurate on the
+// tensor cores (split TF32 operands).
+cudaError_t launch_kupdate_tc(const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains, int max_mp, int k,
+                              int* status, cudaStream_t s);
+bool is_kupdate_tc_kernel(const void* f);
 // Factor chains [0, n_chains) of the given arrays (pointers may be offset to
 // a chain subrange); wmap is the TMA map of Winv; maps16 map the FP16 copies
 // of the off-diagonal L tiles (same layout as M), written by the panel

@@ -51,6 +51,7 @@ struct bd_ctx {
   void* Minv = nullptr;            // FP64 path: 32 x 32 diagonal-block inverses of L, [sum np][32]
   void* Kinv = nullptr;            // 32 x 32 diagonal-block inverses of K's factor, [sum mp][32]
   CUtensorMap* tmaps = nullptr;    // mixed: TMA maps (one per chain matrix, Winv, one per chain FP16 copy)
+  CUtensorMap* kmaps = nullptr;    // mixed: TMA maps of every chain's K
   __half* M16 = nullptr;           // mixed: FP16 copies of the off-diagonal L tiles, layout of M
   double* stage = nullptr;  // staging for host-memory noise / observables
   size_t stage_elems = 0;
@@ -246,7 +247,7 @@ int enqueue_pre_newton_mid_mixed(bd_ctx* c, cudaStream_t s) {
   CK(launch_form_k_pos(c->rmid, (float*)c->K, c->G, c->d_cd, c->n_chains, c->max_m, c->umid, c->ph.hstar,
                        c->ph.a, sk));
   CK(cudaEventRecord(c->aev[6], sk));
-  CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64, c->status, sk));
+  CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->kmaps, c->d_cd, c->n_chains, c->max_mp / 64, c->status, sk));
   CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
   prof_mark(c, 7, sk);
   CK(cudaEventRecord(c->aev[1], sk));
@@ -285,7 +286,7 @@ int enqueue_pre_newton(bd_ctx* c, cudaStream_t s) {
     CK(launch_form_k_pos(c->r, (float*)c->K, c->G, c->d_cd, c->n_chains, c->max_m, c->uhat, c->ph.hstar,
                          c->ph.a, sk));
     CK(cudaEventRecord(c->aev[6], sk));  // the predictor and the first product need only these
-    CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->d_cd, c->n_chains, c->max_mp / 64,
+    CK(launch_chol_k64((float*)c->K, (float*)c->Kinv, c->kmaps, c->d_cd, c->n_chains, c->max_mp / 64,
                        c->status, sk));
     CK(launch_sb_inverse((const float*)c->K, (const float*)c->Kinv, c->Vsb, c->d_cd, c->n_chains, c->max_mp, sk));
   } else {
@@ -663,7 +664,7 @@ void bd_destroy(bd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* bufs[] = {c->d_cd, c->M,     c->K,       c->r,   c->rstar, c->rT,     c->y,
                   c->u,    c->F,     c->uhat,    c->T,   c->rhs,   c->scratch, c->obs,
-                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps,
+                  c->stage, c->status, c->state, c->iters, c->accurate, c->args, c->loops, c->Winv, c->fsplit, c->dT, c->G, c->Vsb, c->M16, c->tmaps, c->kmaps,
                   c->Minv, c->Kinv, c->Md, c->rdot, c->ydot, c->rsdot, c->Gt, c->abase,
                   c->zt, c->DdF, c->DG, c->vt, c->Tdot, c->Fdot, c->rscale, c->kdot, c->rmid, c->umid, c->M2, c->yB, c->zsv, c->rmdot, c->v2, c->zdot};
   for (void* b : bufs)
@@ -820,7 +821,8 @@ int bd_create(const bd_params* p, bd_ctx** out) {
          alloc((void**)&c->dT, rr) && alloc((void**)&c->G, 3 * c->K_elems * sizeof(float)) &&
          alloc((void**)&c->Vsb, (size_t)kwrow * 256 * sizeof(float)) &&
          alloc((void**)&c->M16, c->M_elems * sizeof(__half)) &&
-         alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (2 * c->n_chains + 1));
+         alloc((void**)&c->tmaps, sizeof(CUtensorMap) * (2 * c->n_chains + 1)) &&
+         alloc((void**)&c->kmaps, sizeof(CUtensorMap) * c->n_chains);
   if (ok && c->midpoint)
     ok = alloc((void**)&c->rmid, b3) && alloc((void**)&c->umid, 3 * rr) &&
          (c->mixed || alloc(&c->M2, c->M_elems * sizeof(double)));
@@ -865,6 +867,10 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     if (cudaMemcpy(c->tmaps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         tc_configure() != cudaSuccess)
+      return fail(BD_ERR_CUDA);
+    std::vector<CUtensorMap> km(c->n_chains);
+    if (!make_k_maps(km.data(), (float*)c->K, c->h_cd.data(), c->n_chains) ||
+        cudaMemcpy(c->kmaps, km.data(), sizeof(CUtensorMap) * km.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(BD_ERR_CUDA);
   }
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||

@@ -8,7 +8,9 @@
 //   potrf64 : one CTA factors the 64 x 64 diagonal tile and forms its inverse
 //             (the register-blocked routine of the 128-wide path);
 //   trsm64  : L_ik = A_ik W_kk^T, 64 x 64 per CTA, 8 x 8 outputs per thread;
-//   update64: A_ij -= L_ik L_jk^T for the trailing lower tiles.
+//   update  : A_ij -= L_ik L_jk^T for the trailing lower tiles, on the tensor
+//             cores with split TF32 operands (k_chol_tc.cu), or on the CUDA
+//             cores (update64).
 // The 64 x 64 diagonal-tile inverses are kept for the tension solve.
 #include "bd_internal.h"
 #include "pdl.h"
@@ -165,20 +167,28 @@ cudaError_t k64_configure() {
 }
 
 bool is_k64_kernel(const void* f) {
-  return f == (const void*)k_potrf64 || f == (const void*)k_gemm64<true> || f == (const void*)k_gemm64<false>;
+  return f == (const void*)k_potrf64 || f == (const void*)k_gemm64<true> || f == (const void*)k_gemm64<false> ||
+         is_kupdate_tc_kernel(f);
 }
 
-cudaError_t launch_chol_k64(float* K, float* Kinv, const ChainDesc* cd, int n_chains, int max_tiles,
-                            int* status, cudaStream_t s) {
+// kmaps (TMA maps of every chain's K) selects the tensor-core trailing update
+// (k_chol_tc.cu, split TF32 operands, FP32-accurate); without them the
+// update runs on the CUDA cores (k_gemm64<false>).
+cudaError_t launch_chol_k64(float* K, float* Kinv, const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains,
+                            int max_tiles, int* status, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < max_tiles && e == cudaSuccess; ++k) {
     e = launch_pdl(k_potrf64, dim3(n_chains), dim3(RegPotrf64::kThreads), 0, s, K, Kinv, cd, k, status);
     const int below = max_tiles - 1 - k;
     if (below > 0 && e == cudaSuccess)
       e = launch_pdl(k_gemm64<true>, dim3(below, n_chains), dim3(kG64Threads), g64_smem<true>(), s, K, Kinv, cd, k);
-    if (below > 0 && e == cudaSuccess)
-      e = launch_pdl(k_gemm64<false>, dim3(below * (below + 1) / 2, n_chains), dim3(kG64Threads), g64_smem<false>(),
-                     s, K, Kinv, cd, k);
+    if (below > 0 && e == cudaSuccess) {
+      if (kmaps)
+        e = launch_kupdate_tc(kmaps, cd, n_chains, K64 * max_tiles, k, status, s);
+      else
+        e = launch_pdl(k_gemm64<false>, dim3(below * (below + 1) / 2, n_chains), dim3(kG64Threads),
+                       g64_smem<false>(), s, K, Kinv, cd, k);
+    }
   }
   return e;
 }

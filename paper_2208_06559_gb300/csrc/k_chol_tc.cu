@@ -333,6 +333,173 @@ __global__ void __launch_bounds__(RegPotrf128::kThreads) k_potrf128(float* __res
   if (threadIdx.x == 0 && *reinterpret_cast<const int*>(sm + RegPotrf128::kFlag)) atomicCAS(status + c, BD_OK, BD_ERR_NOT_PD);
 }
 
+// ------------------------------------------------------------ K update
+// Trailing update of the FP32 factorisation of the rod-coupling matrix K
+// (64-wide block columns, k_chol_k64.cu) after block column k:
+// K_ij -= L_ik L_jk^T over 128 x 128 output blocks of the trailing lower
+// triangle (rows and columns from 64 (k + 1); blocks on the diagonal update
+// their lower triangle only), on the tensor cores with FP32 accuracy.  Each
+// operand slice x is split in shared memory into big = tf32(x) and
+// small = tf32(x - big), both rounded to nearest, and the product is formed
+// as small_A big_B + big_A small_B + big_A big_B (kind::tf32, FP32
+// accumulation in TMEM); the dropped small_A small_B is below 2^-22 of it.
+// (K sets the tension iteration's convergence rate and its condition number
+// grows like N^2 for stretched chains, so a plain TF32 product would not
+// do.)  The 64-column panel is taken in two 32-column slices through one
+// 64 KB stage (three CTAs per SM); the result is added into K by TMA
+// reduce-add.
+constexpr int kKuSmem = 4 * kChunkBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+__device__ __forceinline__ void split_tf32(float4* x, float4* xs) {
+  const float4 v = *x;
+  float4 hi, lo;
+  hi.x = tf32_rna(v.x); hi.y = tf32_rna(v.y); hi.z = tf32_rna(v.z); hi.w = tf32_rna(v.w);
+  lo.x = tf32_rna(v.x - hi.x); lo.y = tf32_rna(v.y - hi.y); lo.z = tf32_rna(v.z - hi.z); lo.w = tf32_rna(v.w - hi.w);
+  *x = hi;
+  *xs = lo;
+}
+
+__global__ void __launch_bounds__(128, 3) k_tc_kupdate(const CUtensorMap* __restrict__ kmaps,
+                                                       const ChainDesc* __restrict__ cd, int k,
+                                                       int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 4 * kChunkBytes);
+  uint64_t* done = full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int c = blockIdx.y;
+  const ChainDesc d = cd[c];
+  const int r0 = 64 * (k + 1);
+  if (r0 >= d.mp) return;
+  const int nb = (d.mp - r0 + NB - 1) / NB;
+  const int p = blockIdx.x;
+  if (p >= nb * (nb + 1) / 2) return;
+  int a = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while (a * (a + 1) / 2 > p) --a;
+  while ((a + 1) * (a + 2) / 2 <= p) ++a;
+  const int b = p - a * (a + 1) / 2;
+  const int row0 = r0 + NB * a, col0 = r0 + NB * b;
+  const CUtensorMap* km = kmaps + c;
+
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(done, 1);
+    fence_barrier_init();
+    prefetch_tmap(km);
+  }
+  if (warp == 2) {
+    tmem_alloc(tmem_slot, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  grid_dep_wait();  // the panel L_.k comes from the preceding triangular solve
+
+  uint8_t* sa = smem;
+  uint8_t* sb = smem + kChunkBytes;
+  uint8_t* sas = smem + 2 * kChunkBytes;
+  uint8_t* sbs = smem + 3 * kChunkBytes;
+  constexpr uint32_t idesc = idesc_mma(2u /*tf32*/, 128u, 128u);
+  bool ok = true;
+  for (int q = 0; q < 2 && ok; ++q) {
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(full, 2 * kChunkBytes);
+      tma_load_2d(sa, km, full, 64 * k + 32 * q, row0);
+      tma_load_2d(sb, km, full, 64 * k + 32 * q, col0);
+    }
+    ok = mbar_wait(full, q & 1);
+    if (ok) {
+      float4* xa = reinterpret_cast<float4*>(sa);
+      float4* xb = reinterpret_cast<float4*>(sb);
+      float4* xas = reinterpret_cast<float4*>(sas);
+      float4* xbs = reinterpret_cast<float4*>(sbs);
+#pragma unroll 4
+      for (int e = threadIdx.x; e < kChunkBytes / 16; e += 128) {
+        split_tf32(xa + e, xas + e);
+        split_tf32(xb + e, xbs + e);
+      }
+      fence_proxy_async_smem();
+    }
+    ok = __syncthreads_and(ok) != 0;
+    if (ok && threadIdx.x == 0) {
+      tc_fence_after();
+      const uint64_t ab = desc_sw128(smem_u32(sa)), bb = desc_sw128(smem_u32(sb));
+      const uint64_t as = desc_sw128(smem_u32(sas)), bs = desc_sw128(smem_u32(sbs));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_tf32(tmem, as + 2 * kk, bb + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_tf32(tmem, ab + 2 * kk, bs + 2 * kk, idesc, 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_tf32(tmem, ab + 2 * kk, bb + 2 * kk, idesc, 1u);
+      mma_commit(done);
+    }
+    if (ok) ok = mbar_wait(done, q & 1);  // the stage is free again
+    ok = __syncthreads_and(ok) != 0;
+  }
+  grid_dep_launch();
+
+  // ---- epilogue: -acc (lower triangle of a diagonal block) into K
+  tc_fence_after();
+  float* stage_out = reinterpret_cast<float*>(smem);  // 4 chunks x 16 KiB over the stage
+  const int row = threadIdx.x;
+  const bool diag = (a == b);
+  if (ok) {
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v[32];
+      tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32), v);
+      tmem_ld_wait();
+      float* chunk = stage_out + q * (kChunkBytes / 4) + row * 32;
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        float4 f;
+        float* fp = reinterpret_cast<float*>(&f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int col = 32 * q + 4 * j4 + e;
+          fp[e] = (diag && col > row) ? 0.0f : -__uint_as_float(v[4 * j4 + e]);
+        }
+        *reinterpret_cast<float4*>(chunk + 4 * (j4 ^ (row & 7))) = f;
+      }
+    }
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (ok) {
+      // (mp is a multiple of 64: a 32-column box is wholly inside K or
+      // wholly right of it, and only those inside are issued; rows past mp
+      // are clipped by the TMA unit)
+      for (int q = 0; q < 4; ++q)
+        if (col0 + 32 * q < d.mp) tma_reduce_add_2d(km, stage_out + q * (kChunkBytes / 4), col0 + 32 * q, row0);
+      bulk_commit();
+      bulk_wait_all();
+    } else {
+      atomicCAS(status + c, BD_OK, BD_ERR_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 128);
+  }
+}
+
+bool is_kupdate_tc_kernel(const void* f) { return f == (const void*)k_tc_kupdate; }
+
+cudaError_t launch_kupdate_tc(const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains, int max_mp, int k,
+                              int* status, cudaStream_t s) {
+  const int r0 = 64 * (k + 1);
+  if (r0 >= max_mp) return cudaSuccess;
+  const int nb = (max_mp - r0 + NB - 1) / NB;
+  return launch_pdl(k_tc_kupdate, dim3(nb * (nb + 1) / 2, n_chains), dim3(128), kKuSmem, s, kmaps, cd, k, status);
+}
+
 // ------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -387,10 +554,19 @@ bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, co
   return encode_f32(&host_maps[n_chains], Winv, NB, wrows, NB);
 }
 
+// maps[c]: chain c's FP32 matrix K ([mp][mp]), 32 x 128 boxes.
+bool make_k_maps(CUtensorMap* host_maps, float* K, const ChainDesc* h_cd, int n_chains) {
+  for (int c = 0; c < n_chains; ++c)
+    if (!encode_f32(&host_maps[c], K + h_cd[c].koff, h_cd[c].mp, h_cd[c].mp, h_cd[c].mp)) return false;
+  return true;
+}
+
 cudaError_t tc_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<TC_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_gemm<TC_TRSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_kupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, kKuSmem);
   return e;
 }
 
