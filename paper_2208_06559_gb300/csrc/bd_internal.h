@@ -224,6 +224,16 @@ cudaError_t launch_mob_delta_f32(const double* r, const double* rmid, const doub
                                  double scale, double* y, cudaStream_t s);
 cudaError_t midpoint_configure();
 
+// The whole FP64 rigid-rod step of chains of at most kSmallMaxN beads, one
+// CTA per chain with every matrix in shared memory, all n_steps steps in one
+// launch (k_small.cu).
+constexpr int kSmallMaxN = 32;
+size_t small_smem_bytes(int max_N);
+cudaError_t small_configure(int max_N);
+cudaError_t launch_step_small(double* r, double* T, int* status, int* iters, int* state, const ChainDesc* cd,
+                              int n_chains, int max_N, Phys ph, const double* noise, long long stride,
+                              int n_steps, bool midpoint, cudaStream_t s);
+
 // Mixed-precision tensor-core Cholesky (k_chol_tc.cu).
 bool make_tc_maps(CUtensorMap* host_maps, float* M, float* Winv, __half* M16, const ChainDesc* h_cd,
                   int n_chains);

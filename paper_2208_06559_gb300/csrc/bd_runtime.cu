@@ -87,6 +87,8 @@ struct bd_ctx {
   bool have_state = false;
   int direct_iters = 0;  // > 0: launch the step's kernels directly (profiling), no graph
   int graph_unroll = 0;  // tension iterations captured as plain graph nodes before the WHILE node
+  bool small = false;    // FP64 rigid rods, every chain <= kSmallMaxN beads: the fused step (k_small.cu)
+  unsigned long long small_launches = 0;
   int while_cap = 1;     // WHILE-node iterations allowed per step
   cudaEvent_t* prof = nullptr;  // bd_profile_step: stage-boundary events
   bool fraenkel = false;        // BD_FRAENKEL: semi-implicit spring update instead of the tension solve
@@ -873,6 +875,12 @@ int bd_create(const bd_params* p, bd_ctx** out) {
         cudaMemcpy(c->kmaps, km.data(), sizeof(CUtensorMap) * km.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(BD_ERR_CUDA);
   }
+  // The fused step takes FP64 rigid-rod batches of short chains (BD_SMALL_STEP=0
+  // keeps them on the multi-kernel step, for comparisons).
+  c->small = !c->mixed && !c->fraenkel && c->max_N <= kSmallMaxN;
+  if (const char* e = getenv("BD_SMALL_STEP"))
+    if (atoi(e) == 0) c->small = false;
+  if (c->small && small_configure(c->max_N) != cudaSuccess) return fail(BD_ERR_CUDA);
   if (matvec_configure() != cudaSuccess || tension_configure() != cudaSuccess ||
       assemble_configure() != cudaSuccess || refine_configure() != cudaSuccess ||
       k64_configure() != cudaSuccess || gmode_configure() != cudaSuccess ||
@@ -936,7 +944,7 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = c->direct_iters > 0 ? BD_OK : build_step_graph(c);
+  int rc = (c->direct_iters > 0 || c->small) ? BD_OK : build_step_graph(c);
   if (rc) return rc;
   const long long stride = c->total_beads * 3;
   const double* nz = noise;
@@ -945,6 +953,20 @@ int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
     CK(cudaMemcpyAsync(c->stage, noise, (size_t)stride * n_steps * sizeof(double),
                        cudaMemcpyHostToDevice, s));
     nz = c->stage;
+  }
+  if (c->small && c->direct_iters == 0) {
+    // short FP64 chains: the fused step, all n_steps in one launch on the
+    // context's stream (fenced against the caller's stream like the graph)
+    cudaStream_t cs = c->cs;
+    CK(cudaEventRecord(c->aev[4], s));
+    CK(cudaStreamWaitEvent(cs, c->aev[4], 0));
+    CK(launch_step_small(c->r, c->T, c->status, c->iters, c->state, c->d_cd, c->n_chains, c->max_N, c->ph, nz,
+                         stride, n_steps, c->midpoint, cs));
+    c->small_launches += 1;
+    c->steps_launched += (unsigned long long)n_steps;
+    CK(cudaEventRecord(c->aev[5], cs));
+    CK(cudaStreamWaitEvent(s, c->aev[5], 0));
+    return BD_OK;
   }
   CK(launch_set_args(c->args, nz, stride, n_steps, s));
   // The steps run on the context's highest-priority stream, ordered after the
@@ -1011,8 +1033,9 @@ int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
   CK(cudaMemcpyAsync(&loops, c->loops, sizeof(loops), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   // set_args launches once per bd_step call; it is not counted here
-  *out = c->steps_launched * (unsigned long long)c->graph_kernels +
-         loops * (unsigned long long)c->body_kernels;
+  *out = c->small ? c->small_launches
+                  : c->steps_launched * (unsigned long long)c->graph_kernels +
+                        loops * (unsigned long long)c->body_kernels;
   return BD_OK;
 }
 
