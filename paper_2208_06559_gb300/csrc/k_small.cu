@@ -78,13 +78,14 @@ __device__ __forceinline__ void tri_pair(int e, int& i, int& k) {
 
 // D (full, both triangles, row pitch p) of the N beads at r.
 __device__ void assemble_small(const double* r, int N, double hstar, double a, double* D, int p) {
+  const double inv_a = 1.0 / a;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i = e / N, j = e % N;
     double R[3] = {0.0, 0.0, 0.0}, cI = 1.0, cRR = 0.0;
     if (i != j) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) R[q] = r[3 * i + q] - r[3 * j + q];
-      rpy_coeffs<double>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, a, cI, cRR);
+      rpy_coeffs_inv<double>(R[0] * R[0] + R[1] * R[1] + R[2] * R[2], hstar, a, inv_a, cI, cRR);
     }
 #pragma unroll
     for (int x = 0; x < 3; ++x)

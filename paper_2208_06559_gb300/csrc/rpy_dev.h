@@ -24,6 +24,35 @@ __device__ __forceinline__ void rpy_coeffs(C R2, C hstar, C a, C& cI, C& cRR) {
   }
 }
 
+// The same coefficients from one square root and one division (the inverse
+// distance; every other quotient becomes a product), for FP64 code where each
+// division or square root is a long instruction sequence: the same values up
+// to the last bits of the rounding.  inv_a = 1 / a.
+template <typename C>
+__device__ __forceinline__ void rpy_coeffs_inv(C R2, C hstar, C a, C inv_a, C& cI, C& cRR) {
+  if (hstar == C(0)) {
+    cI = C(0);
+    cRR = C(0);
+    return;
+  }
+  if (R2 > C(0)) {
+    const C iR = C(1) / sqrt(R2), iR2 = iR * iR;
+    if (R2 >= C(4) * a * a) {  // R >= 2a
+      const C pref = C(0.75) * hstar * iR;
+      const C a2R2 = a * a * iR2;
+      cI = pref * (C(1) + C(2) / C(3) * a2R2);
+      cRR = pref * (C(1) - C(2) * a2R2) * iR2;
+    } else {
+      const C pref = C(0.375) * hstar * inv_a;
+      cI = pref * (C(8) / C(3) - C(0.75) * (R2 * iR) * inv_a);
+      cRR = pref * (C(0.25) * inv_a) * iR;
+    }
+  } else {
+    cI = C(0.375) * hstar * inv_a * (C(8) / C(3));
+    cRR = C(0);
+  }
+}
+
 // The same coefficients in FP32 from one reciprocal square root (rsqrtf, a
 // few ulp) and a precomputed 1 / a instead of a square root and three
 // divisions: a relative change of order 1e-7, the size of the FP32 rounding

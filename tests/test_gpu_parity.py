@@ -267,18 +267,19 @@ def test_one_graph_launch_runs_every_step(bd, monkeypatch, precision, unroll):
         assert np.abs(d - dr).max() <= 1e-3 * np.abs(dr).max(), np.abs(d - dr).max()
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
-def test_fused_short_chain_step_equals_multi_kernel_step(bd, monkeypatch, scheme):
+@pytest.mark.parametrize("scheme,hstar", [(0, 0.25), (1, 0.25), (0, 0.6)])
+def test_fused_short_chain_step_equals_multi_kernel_step(bd, monkeypatch, scheme, hstar):
     """FP64 batches whose chains have at most 32 beads take the fused step
     (one CTA per chain, every matrix in shared memory, all the steps of a
     call in one launch).  On an uneven batch under shear, 20 steps of it
     match 20 steps of the multi-kernel step (BD_SMALL_STEP=0) to round-off,
     with the same status words and tension iteration counts within one, in
-    one kernel launch per call; both match the oracle."""
+    one kernel launch per call; both match the oracle.  h* = a = 0.6 puts
+    bonded beads inside 2a (the overlap branch of the RPY tensor)."""
     Nc = np.array([2, 3, 16, 31, 32], np.int32)
     r0 = inputs.random_walk(Nc, 41)
     noise = inputs.gaussian_noise(20, int(Nc.sum()), 42)
-    kw = dict(h_star=0.25, dt=1e-3, flow=bd.FLOW_SHEAR, Wi=5.0, scheme=scheme)
+    kw = dict(h_star=hstar, a=hstar, dt=1e-3, flow=bd.FLOW_SHEAR, Wi=5.0, scheme=scheme)
     out = {}
     for fused in (True, False):
         if not fused:
@@ -295,7 +296,7 @@ def test_fused_short_chain_step_equals_multi_kernel_step(bd, monkeypatch, scheme
     assert np.abs(ra - rb).max() <= 1e-12 * np.abs(rb).max()
     assert np.abs(ia.astype(int) - ib.astype(int)).max() <= 1, (ia, ib)
     assert la == 1 and lb > 100, (la, lb)
-    p = orc.make_params(hstar=0.25, dt=1e-3, flow=orc.FLOW_SHEAR, Wi=5.0, scheme=scheme)
+    p = orc.make_params(hstar=hstar, a=hstar, dt=1e-3, flow=orc.FLOW_SHEAR, Wi=5.0, scheme=scheme)
     rr, _, st_ref, _, _ = orc.run(p, Nc, r0, noise)
     assert (st_ref == 0).all()
     assert np.abs(ra - rr).max() <= 1e-10 * np.abs(rr).max()
