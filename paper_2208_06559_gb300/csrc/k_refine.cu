@@ -129,8 +129,8 @@ __device__ __forceinline__ void trsv_cp16(float* smem, const float* gmem) {
                : "memory");
 }
 
-// The solve is split over a cluster of CL CTAs per chain (CL = 2 for
-// np <= 12288, 4 up to 24576): CTA `rank` owns the columns of the 128-wide
+// The solve is split over a cluster of CL CTAs per chain (trsv_cluster: 2, 4
+// or 8, at least 2 for np <= 12288 and 4 up to 24576): CTA `rank` owns the columns of the 128-wide
 // blocks B with B % CL == rank (local column l = t + 1024 q -> block
 // CL (l / 128) + rank).  For block b the owner publishes its 128 accumulated
 // sums through distributed shared memory, every CTA forms z_b (the same
@@ -138,6 +138,20 @@ __device__ __forceinline__ void trsv_cp16(float* smem, const float* gmem) {
 // the columns it owns.  W_{b-1} is copied (cp.async) into the other half of a
 // double buffer while block b is processed.  Rank 0 writes z.
 constexpr int kTrsvColsCl = 6;  // owned columns per thread: np <= 6144 CL
+
+// Cluster size of the solve: the smallest that holds np (2 up to np = 12288,
+// 4 up to 24576), doubled up to 8 while the solve's CTAs (one per SM, every
+// chain a cluster) would fill at most three quarters of the SMs -- a small
+// batch of long chains then streams its factor through more SMs; the rest
+// stay free for the product L~ xi that runs beside it.
+static int g_trsv_sms = 0;
+
+static int trsv_cluster(int n_chains, int max_np) {
+  int cl = max_np <= 2 * kTrsvColsCl * kTrsvThreads ? 2 : 4;
+  const long long budget = (long long)(g_trsv_sms > 0 ? g_trsv_sms : 148) * 3 / 4;
+  while (cl < 8 && (long long)n_chains * 2 * cl <= budget) cl *= 2;
+  return cl;
+}
 
 template <int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kTrsvThreads)
@@ -286,10 +300,11 @@ cudaError_t launch_brownian_f32_begin(const float* M, const float* Winv, const C
   cudaError_t e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev[0], 0);
   if (e != cudaSuccess) return e;
-  if (max_np <= 2 * 6 * kTrsvThreads)
-    k_trsv_t_f32c<2><<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
-  else
-    k_trsv_t_f32c<4><<<4 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z);
+  switch (trsv_cluster(n_chains, max_np)) {
+    case 2: k_trsv_t_f32c<2><<<2 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z); break;
+    case 4: k_trsv_t_f32c<4><<<4 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z); break;
+    default: k_trsv_t_f32c<8><<<8 * n_chains, kTrsvThreads, kTrsvSmem, s2>>>(M, Winv, cd, x, args, z); break;
+  }
   if (refine)
     k_trmv_f32<<<dim3(ceil_div(max_np, 32), n_chains), 256, 0, s>>>(M, cd, scratch, 1.0, y1);
   else
@@ -325,8 +340,11 @@ cudaError_t launch_brownian_f32(const float* M, const float* Winv, const ChainDe
 }
 
 cudaError_t refine_configure() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_trsv_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaFuncSetAttribute(k_trsv_t_f32c<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_trsv_t_f32c<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_trsv_t_f32c<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsvSmem);
   return e;
 }
 
