@@ -11,10 +11,11 @@
 //   forward  z_S = V_S (rhs_S - L[S, 0:256S] z)
 //   backward x_S = V_S^T (z_S - L[256(S+1):m, S]^T x)
 // Each super-step is two passes of independent 16-byte loads over all
-// threads of a two-CTA cluster (the off-diagonal part split by alternate
-// 64-wide column blocks or alternate rows, the V_S product by alternate
-// rows), with the partial results exchanged through distributed shared
-// memory and combined in a fixed order, so both CTAs hold identical z and x.
+// threads of a cluster of CL CTAs (2, 4 or 8; the off-diagonal part split by
+// 64-wide column blocks or rows taken round-robin, the V_S product by rows
+// round-robin), with the partial results exchanged through distributed
+// shared memory and combined in rank order, so every CTA holds identical z
+// and x.
 // Rank 0 writes T += x, the update itself (for the incremental rod-space
 // products) and F(T).
 #include <cooperative_groups.h>
@@ -138,7 +139,18 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
+// Sum over the cluster's CTAs of their partial results p[t] (distributed
+// shared memory), in rank order in every CTA, so that all hold the same value.
+template <int CL>
+__device__ __forceinline__ float cluster_sum(cooperative_groups::cluster_group& cl, float* p, int rank, int t) {
+  float s = 0.0f;
+#pragma unroll
+  for (int q = 0; q < CL; ++q) s += (q == rank) ? p[t] : cl.map_shared_rank(p, q)[t];
+  return s;
+}
+
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSbThreads)
     k_newton_solve_sb(const float* __restrict__ K, const float* __restrict__ V,
                       const ChainDesc* __restrict__ cd, Phys ph, const double* __restrict__ uhat,
                       const double* __restrict__ rhs, double* __restrict__ Tn, double* __restrict__ F,
@@ -152,7 +164,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
   __shared__ __align__(16) float red[16][kSB];
   __shared__ __align__(16) float xb[2][kSB];  // exchanged partial results, by exchange parity
   __shared__ __align__(16) float sv[kSB];
-  const int c = blockIdx.x >> 1;
+  const int c = blockIdx.x / CL;
   grid_dep_wait();
   const int st = state[c];
   if (st != NS_ACTIVE && st != NS_EXTRA) return;  // the same for both CTAs of the cluster
@@ -175,14 +187,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
     const int nbj = R0 / 64;  // column blocks left of the super-block
     {
       const int half = lane >> 4, q = lane & 15;
-      // rows r and r + 32 together; this CTA's column blocks j = rank, rank + 2, ...
+      // rows r and r + 32 together; this CTA's column blocks j = rank, rank + CL, ...
       for (int r = warp; r < nS; r += 64) {
         const int r2 = r + 32;
         const float* La = L + (long long)(R0 + r) * mp + 4 * q;
         const float* Lb = L + (long long)(R0 + (r2 < nS ? r2 : r)) * mp + 4 * q;
         float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll 2
-        for (int j = rank + 2 * half; j < nbj; j += 4) {
+        for (int j = rank + CL * half; j < nbj; j += 2 * CL) {
           const float4 la = __ldg(reinterpret_cast<const float4*>(La + 64 * j));
           const float4 lb = __ldg(reinterpret_cast<const float4*>(Lb + 64 * j));
           const float4 zv = *reinterpret_cast<const float4*>(zs + 64 * j + 4 * q);
@@ -200,20 +212,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
     cl.sync();
     if (t < kSB) {
       float s = 0.0f;
-      if (t < nS) {
-        const float own = xb[ex & 1][t];
-        const float oth = cl.map_shared_rank(&xb[ex & 1][0], rank ^ 1)[t];
-        s = bs[R0 + t] - (rank == 0 ? own + oth : oth + own);
-      }
+      if (t < nS) s = bs[R0 + t] - cluster_sum<CL>(cl, &xb[ex & 1][0], rank, t);
       sv[t] = s;
     }
     ++ex;
     __syncthreads();
     {
-      // z_S = V_S s, rows r = 2 k + rank; row r has nonzeros in columns <= r
+      // z_S = V_S s, rows r = CL k + rank; row r has nonzeros in columns <= r
       const float* VS = Vc + (long long)R0 * kSB;
-      for (int k = warp; 2 * k + rank < nS; k += 32) {
-        const int r = 2 * k + rank;
+      for (int k = warp; CL * k + rank < nS; k += 32) {
+        const int r = CL * k + rank;
         const float* Vr = VS + (long long)r * kSB;
         const int n4 = 16 * (r / 64 + 1);
         float a = 0.0f;
@@ -225,8 +233,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
       }
     }
     cl.sync();
-    if (t < nS)
-      zs[R0 + t] = ((t & 1) == rank) ? xb[ex & 1][t] : cl.map_shared_rank(&xb[ex & 1][0], rank ^ 1)[t];
+    if (t < nS) {
+      const int owner = t % CL;
+      zs[R0 + t] = owner == rank ? xb[ex & 1][t] : cl.map_shared_rank(&xb[ex & 1][0], owner)[t];
+    }
     ++ex;
     __syncthreads();
   }
@@ -239,7 +249,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
     if (C0 + 4 * cq < mp) {
       const float* Lc = L + C0 + 4 * cq;
 #pragma unroll 4
-      for (int R = R1 + 2 * rl + rank; R < m; R += 32) {
+      for (int R = R1 + CL * rl + rank; R < m; R += 16 * CL) {
         const float4 lv = __ldg(reinterpret_cast<const float4*>(Lc + (long long)R * mp));
         const float xr = zs[R];
         acc.x = fmaf(lv.x, xr, acc.x);
@@ -259,21 +269,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
     cl.sync();
     if (t < kSB) {
       float s = 0.0f;
-      if (t < nS) {
-        const float own = xb[ex & 1][t];
-        const float oth = cl.map_shared_rank(&xb[ex & 1][0], rank ^ 1)[t];
-        s = zs[C0 + t] - (rank == 0 ? own + oth : oth + own);
-      }
+      if (t < nS) s = zs[C0 + t] - cluster_sum<CL>(cl, &xb[ex & 1][0], rank, t);
       sv[t] = s;
     }
     ++ex;
     __syncthreads();
-    // x_S = V_S^T s over rows r = 2 (rl + 16 i) + rank; V_S[r][c] = 0 for c > r
+    // x_S = V_S^T s over rows r = CL (rl + 16 i) + rank; V_S[r][c] = 0 for c > r
     acc = make_float4(0.f, 0.f, 0.f, 0.f);
     {
       const float* VS = Vc + (long long)C0 * kSB + 4 * cq;
 #pragma unroll 4
-      for (int r = 2 * rl + rank; r < nS; r += 32) {
+      for (int r = CL * rl + rank; r < nS; r += 16 * CL) {
         if (4 * cq <= r) {
           const float4 v = __ldg(reinterpret_cast<const float4*>(VS + (long long)r * kSB));
           const float sr = sv[r];
@@ -293,11 +299,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSbThreads)
       xb[ex & 1][t] = p;
     }
     cl.sync();
-    if (t < nS) {
-      const float own = xb[ex & 1][t];
-      const float oth = cl.map_shared_rank(&xb[ex & 1][0], rank ^ 1)[t];
-      zs[C0 + t] = rank == 0 ? own + oth : oth + own;
-    }
+    if (t < nS) zs[C0 + t] = cluster_sum<CL>(cl, &xb[ex & 1][0], rank, t);
     ++ex;
     __syncthreads();
   }
@@ -328,20 +330,45 @@ cudaError_t launch_sb_inverse(const float* K, const float* Kinv, float* V, const
                     cd);
 }
 
+// Cluster size of the solve: 2 CTAs per chain, doubled up to 8 while the
+// solve's CTAs would fill at most three quarters of the SMs (a small batch
+// of long chains streams K's factor through more SMs).
+static int g_sb_sms = 0;
+
+static int sb_cluster(int n_chains) {
+  int cl = 2;
+  const long long budget = (long long)(g_sb_sms > 0 ? g_sb_sms : 148) * 3 / 4;
+  while (cl < 8 && (long long)n_chains * 2 * cl <= budget) cl *= 2;
+  return cl;
+}
+
 cudaError_t launch_newton_solve_sb(const float* K, const float* V, const ChainDesc* cd, int n_chains, Phys ph,
                                    const double* uhat, const double* rhs, double* Tn, double* F, int* state,
                                    int* iters, double* dT, cudaStream_t s) {
-  return launch_pdl(k_newton_solve_sb, dim3(2 * n_chains), dim3(kSbThreads), 2 * kSbMaxM * sizeof(float), s, K, V,
-                    cd, ph, uhat, rhs, Tn, F, state, iters, dT);
+  const size_t smem = 2 * kSbMaxM * sizeof(float);
+  switch (sb_cluster(n_chains)) {
+    case 2:
+      return launch_pdl(k_newton_solve_sb<2>, dim3(2 * n_chains), dim3(kSbThreads), smem, s, K, V, cd, ph, uhat, rhs,
+                        Tn, F, state, iters, dT);
+    case 4:
+      return launch_pdl(k_newton_solve_sb<4>, dim3(4 * n_chains), dim3(kSbThreads), smem, s, K, V, cd, ph, uhat, rhs,
+                        Tn, F, state, iters, dT);
+    default:
+      return launch_pdl(k_newton_solve_sb<8>, dim3(8 * n_chains), dim3(kSbThreads), smem, s, K, V, cd, ph, uhat, rhs,
+                        Tn, F, state, iters, dT);
+  }
 }
 
 bool is_sb_inverse_kernel(const void* f) { return f == (const void*)k_sb_inverse; }
 
 cudaError_t solve_sb_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_sb_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kSbInvSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_newton_solve_sb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * kSbMaxM * sizeof(float)));
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sb_sms, cudaDevAttrMultiProcessorCount, dev);
+  const int smem = (int)(2 * kSbMaxM * sizeof(float));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_newton_solve_sb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_newton_solve_sb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_newton_solve_sb<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
