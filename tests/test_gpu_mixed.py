@@ -222,6 +222,32 @@ def test_rod_space_iteration_without_hi_matches_fp64(bd):
     assert err < 1e-6, err
 
 
+def test_sixteen_chain_batch_against_fp64(bd):
+    """16 chains select 4-CTA clusters for the refinement's triangular solve
+    and the tension solve (2 CTAs for larger batches, 8 for smaller): two
+    steps of shear Wi = 100 with HI, mixed against FP64 on the same noise --
+    every chain converges within the FP64 iteration count + 2, rods hold to
+    1e-10, displacements agree to the factor's first-order error (1e-3)."""
+    Nc = np.array([300, 257, 129, 400] * 4, np.int32)
+    r0 = inputs.random_walk(Nc, 57)
+    noise = cuda(inputs.gaussian_noise(2, int(Nc.sum()), 58))
+    out, its = {}, {}
+    for prec in (bd.FP64, bd.MIXED_TF32):
+        ctx = bd.Context(Nc, precision=prec, flow=1, Wi=100.0)
+        ctx.set_state(cuda(r0))
+        ctx.step(noise)
+        obs, st = ctx.observables()
+        assert (st == 0).all(), (prec, st)
+        assert obs[:, bd.OBS_MAXDEV].max().item() < 1e-10
+        out[prec] = ctx.get_state().cpu().numpy()
+        its[prec] = ctx.chain_status()[1]
+        ctx.close()
+    assert (its[bd.MIXED_TF32] <= its[bd.FP64] + 2).all(), (its[bd.MIXED_TF32], its[bd.FP64])
+    d64 = out[bd.FP64] - r0
+    err = np.abs(out[bd.MIXED_TF32] - out[bd.FP64]).max() / np.abs(d64).max()
+    assert err < 1e-3, err
+
+
 def test_rod_space_iteration_edge_sizes_with_hi(bd):
     """With hydrodynamic interactions at the same edge sizes: every chain
     converges within the FP64 path's iteration count + 2, rods hold to
