@@ -120,11 +120,18 @@ typedef struct {
   int refine;            /* mixed precision: 1 = one refinement step on B xi */
   double k_spring;       /* BD_FRAENKEL: spring constant K* > 0 (Eq. (3)); unused for BD_RIGID */
   int scheme;            /* bd_scheme of the rigid-rod step (BD_RIGID only) */
+  int lanes;             /* mixed precision: concurrent sub-batches (lanes) the chains are split into,
+                            contiguous ranges of about equal factorisation work, each stepped by its
+                            own graph on its own streams; 0 = automatic (2 from 32 chains, or from
+                            4 chains when one has >= 2000 beads; else 1), 1..8 (at most n_chains);
+                            FP64 contexts always use 1.  A chain's result depends on the lanes only
+                            through the shapes chosen for its per-chain kernels (summation order).
+                            Out of range: BD_ERR_ARG */
 } bd_params;
 
 /* Fill *p with defaults: 1 chain (n_beads NULL), h* = 0.25, a = h*, dt = 1e-4,
  * no flow, lambda = 1, BD_FP64, BD_RIGID, tol 1e-13, max_newton 50, refine 1,
- * k_spring 1e4, BD_SCHEME_MIDPOINT. */
+ * k_spring 1e4, BD_SCHEME_MIDPOINT, lanes 0 (automatic). */
 void bd_params_default(bd_params* p);
 
 /* Create a context on the current CUDA device: validates *p, copies n_beads,
@@ -148,7 +155,10 @@ int bd_get_state(bd_ctx* ctx, double* r_dev, void* stream);
  * read during the call's stream work (host memory is copied before return of
  * the staged copies).  All n_steps run in one launch of the context's CUDA
  * graph, whose outer WHILE node loops over the steps on the device (the
- * first call captures and instantiates the graph).  Asynchronous; returns
+ * first call captures and instantiates the graph); a context with lanes
+ * launches every lane's graph on the lane's own stream, all waiting for the
+ * caller's earlier work on `stream`, and the caller's later work on it waits
+ * for all of them.  Asynchronous; returns
  * BD_OK unless the arguments or a CUDA call fail.  Errors: BD_ERR_ARG,
  * BD_ERR_STATE, BD_ERR_CUDA. */
 int bd_step(bd_ctx* ctx, int n_steps, const double* noise, void* stream);
@@ -174,14 +184,16 @@ int bd_chain_status(bd_ctx* ctx, int* status_host, int* newton_host, void* strea
  * commit, whole step, and the end of the K chain measured from the start of
  * the step.  The state advances by one step as with bd_step.  It runs on the
  * context's own stream, where bd_step runs too; work the caller enqueued on
- * other streams must be complete.  Synchronises the context's stream.  Errors: BD_ERR_ARG (NULL or host noise),
+ * other streams must be complete.  Synchronises the context's stream.  A
+ * context with lanes profiles them one after another and reports the sums of
+ * their times.  Errors: BD_ERR_ARG (NULL or host noise),
  * BD_ERR_STATE (no state), BD_ERR_CUDA. */
 int bd_profile_step(bd_ctx* ctx, const double* noise, int newton_iters, double* ms_out);
 
 /* Number of kernel launches executed by bd_step on this context since its
  * creation (the kernels of one step of the captured graph times the steps,
- * plus the kernels of every executed tension-solve iteration).  Synchronises the
- * stream. */
+ * plus the kernels of every executed tension-solve iteration), summed over
+ * the lanes.  Synchronises the stream. */
 int bd_kernel_launches(bd_ctx* ctx, unsigned long long* out, void* stream);
 
 /* Diagnostic: ||B B^T - D||_F / ||D||_F for one chain, from the factor and
@@ -227,7 +239,7 @@ int bd_midpoint(bd_ctx* ctx, const double* xi_dev, double* rmid_dev, double* y_d
  * left at the final state.  With BD_SCHEME_MIDPOINT the tangents also run
  * through the midpoint: z' = -L^{-T} Phi(X)^T xi, the derivative of the
  * tangent-space projection, and D(r_m)' from r_m'.  FP64 rigid-rod contexts
- * with h* > 0 only (else BD_ERR_ARG).
+ * with h* > 0 only (else BD_ERR_ARG; such contexts have one lane).
  * Synchronises the stream; returns the most severe chain status. */
 int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noise_dev,
                int ckpt_every, const double* dJdr_final_dev, double grad_host[2], void* stream);
@@ -245,7 +257,10 @@ int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noi
  * bd_set_factor_config applies a known choice (e.g. from a cache).  Both drop
  * the captured step graph, which is rebuilt by the next bd_step.  Mixed
  * contexts only (BD_ERR_ARG otherwise); bd_tune_factor needs bd_set_state
- * first and synchronises the stream. */
+ * first and synchronises the stream.  With lanes, each shape is timed with
+ * every lane factoring its chains concurrently and the winner is applied to
+ * every lane; bd_set_factor_config also applies to every lane (groups are
+ * per lane). */
 int bd_tune_factor(bd_ctx* ctx, int* panel_out, int* groups_out, double* ms_out, void* stream);
 int bd_set_factor_config(bd_ctx* ctx, int panel, int groups);  /* 1 <= panel <= 96 */
 

@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("refine", ctypes.c_int),
         ("k_spring", ctypes.c_double),
         ("scheme", ctypes.c_int),
+        ("lanes", ctypes.c_int),
     ]
 
 
@@ -193,7 +194,7 @@ class Context:
                  flow: int = FLOW_NONE, Wi: float = 0.0, lam: float = 1.0, a: float = 0.0,
                  precision: int = FP64, tol: float = 1e-13, max_newton: int = 50,
                  refine: int = 1, constraint: int = RIGID, k_spring: float = 1e4,
-                 scheme: int = SCHEME_MIDPOINT):
+                 scheme: int = SCHEME_MIDPOINT, lanes: int = 0):
         import torch
         L = lib()
         # the library's current device at creation (without CUDA, bd_create reports the error)
@@ -210,6 +211,7 @@ class Context:
         p.flow, p.Wi, p.lambda_ = int(flow), float(Wi), float(lam)
         p.precision, p.tol, p.max_newton, p.refine = int(precision), float(tol), int(max_newton), int(refine)
         p.constraint, p.k_spring, p.scheme = int(constraint), float(k_spring), int(scheme)
+        p.lanes = int(lanes)
         h = ctypes.c_void_p()
         _check(L.bd_create(ctypes.byref(p), ctypes.byref(h)), "bd_create")
         self._h = h

@@ -24,6 +24,10 @@
 
 using namespace bd;
 
+struct bd_ctx;
+using lanes_t = std::vector<bd_ctx*>;
+constexpr int kMaxLanes = 8;
+
 struct bd_ctx {
   int device = 0;
   bd_params p{};
@@ -96,6 +100,14 @@ struct bd_ctx {
   double* rmid = nullptr;       // midpoint positions r_m, [sum N][3]
   double* umid = nullptr;       // unit rod directions of r_m, [sum (N-1)][3]
   void* M2 = nullptr;           // FP64 midpoint path: D(r_m), full symmetric, layout of M
+  // lanes: a mixed-precision context of many chains holds sub-contexts over
+  // contiguous chain ranges whose steps run concurrently on their own
+  // streams; the parent holds no device workspace but the noise staging
+  lanes_t lanes;
+  std::vector<int> lane_c0;             // first chain of each lane (+ n_chains)
+  std::vector<long long> lane_b0;       // first bead of each lane
+  std::vector<long long> lane_r0;       // first rod of each lane
+  cudaEvent_t fork = nullptr;           // caller-stream event every lane's steps wait for
   std::mutex mu;
 };
 
@@ -659,7 +671,7 @@ const char* bd_strerror(int code) {
   }
 }
 
-void bd_destroy(bd_ctx* c) {
+static void ctx_destroy(bd_ctx* c) {
   if (!c) return;
   DeviceGuard g(c->device);
   if (c->exec) cudaGraphExecDestroy(c->exec);
@@ -684,10 +696,10 @@ void bd_destroy(bd_ctx* c) {
   delete c;
 }
 
-int bd_create(const bd_params* p, bd_ctx** out) {
-  if (!out) return BD_ERR_ARG;
-  *out = nullptr;
+// Checks every field of *p; no device call.
+static int validate_params(const bd_params* p) {
   if (!p || p->n_chains < 1 || !p->n_beads) return BD_ERR_ARG;
+  if (p->lanes < 0 || p->lanes > kMaxLanes) return BD_ERR_ARG;
   if (!(p->dt > 0.0) || !(p->h_star >= 0.0)) return BD_ERR_ARG;
   if (!std::isfinite(p->dt) || !std::isfinite(p->h_star) || !std::isfinite(p->Wi) ||
       !std::isfinite(p->lambda) || !std::isfinite(p->tol))
@@ -708,6 +720,15 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   const int max_beads = (p->precision == BD_FP64) ? 4096 : 8192;
   for (int i = 0; i < p->n_chains; ++i)
     if (p->n_beads[i] < 2 || p->n_beads[i] > max_beads) return BD_ERR_ARG;
+  return BD_OK;
+}
+
+// One context over all of p's chains (no lanes).
+static int ctx_create(const bd_params* p, bd_ctx** out) {
+  if (!out) return BD_ERR_ARG;
+  *out = nullptr;
+  if (int rc = validate_params(p)) return rc;
+  const double a = p->a > 0.0 ? p->a : p->h_star;
 
   bd_ctx* c = new (std::nothrow) bd_ctx();
   if (!c) return BD_ERR_OOM;
@@ -829,11 +850,11 @@ int bd_create(const bd_params* p, bd_ctx** out) {
     ok = alloc((void**)&c->rmid, b3) && alloc((void**)&c->umid, 3 * rr) &&
          (c->mixed || alloc(&c->M2, c->M_elems * sizeof(double)));
   if (!ok) {
-    bd_destroy(c);
+    ctx_destroy(c);
     return BD_ERR_OOM;
   }
   auto fail = [&](int code) {
-    bd_destroy(c);
+    ctx_destroy(c);
     return code;
   };
   // Stream priorities: the factorisation's latency-bound chain (main and
@@ -916,7 +937,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   return BD_OK;
 }
 
-int bd_set_state(bd_ctx* c, const double* r_dev, void* stream) {
+static int ctx_set_state(bd_ctx* c, const double* r_dev, void* stream) {
   if (!c || !r_dev) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -929,7 +950,7 @@ int bd_set_state(bd_ctx* c, const double* r_dev, void* stream) {
   return BD_OK;
 }
 
-int bd_get_state(bd_ctx* c, double* r_dev, void* stream) {
+static int ctx_get_state(bd_ctx* c, double* r_dev, void* stream) {
   if (!c || !r_dev) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
@@ -938,57 +959,65 @@ int bd_get_state(bd_ctx* c, double* r_dev, void* stream) {
   return BD_OK;
 }
 
-int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
+// Runs n_steps on the context's stream c->cs once `start` has completed and
+// records c->aev[5] at their end; nz: the noise of the context's first bead
+// in step 0, step k at nz + k stride.  The caller holds c->mu.
+static int launch_steps_locked(bd_ctx* c, int n_steps, const double* nz, long long stride, cudaEvent_t start) {
+  int rc = (c->direct_iters > 0 || c->small) ? BD_OK : build_step_graph(c);
+  if (rc) return rc;
+  cudaStream_t cs = c->cs;
+  CK(cudaStreamWaitEvent(cs, start, 0));
+  if (c->small && c->direct_iters == 0) {
+    // short FP64 chains: the fused step, all n_steps in one launch
+    CK(launch_step_small(c->r, c->T, c->status, c->iters, c->state, c->d_cd, c->n_chains, c->max_N, c->ph, nz,
+                         stride, n_steps, c->midpoint, cs));
+    c->small_launches += 1;
+    c->steps_launched += (unsigned long long)n_steps;
+  } else {
+    CK(launch_set_args(c->args, nz, stride, n_steps, cs));
+    if (c->direct_iters > 0) {
+      for (int i = 0; i < n_steps; ++i)
+        if ((rc = enqueue_step_direct(c, cs))) return rc;
+    } else {
+      CK(cudaGraphLaunch(c->exec, cs));  // all n_steps steps in one launch
+      c->steps_launched += (unsigned long long)n_steps;
+    }
+  }
+  CK(cudaEventRecord(c->aev[5], cs));
+  return BD_OK;
+}
+
+// Copies host-memory noise of n_steps steps to the context's staging buffer
+// on stream s; *nz receives the device address to read.
+static int stage_noise(bd_ctx* c, int n_steps, const double* noise, cudaStream_t s, const double** nz) {
+  const long long stride = c->total_beads * 3;
+  *nz = noise;
+  if (is_device_ptr(noise)) return BD_OK;
+  if (int rc = ensure_stage(c, (size_t)stride * n_steps)) return rc;
+  CK(cudaMemcpyAsync(c->stage, noise, (size_t)stride * n_steps * sizeof(double), cudaMemcpyHostToDevice, s));
+  *nz = c->stage;
+  return BD_OK;
+}
+
+static int ctx_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
   if (!c || n_steps < 1 || !noise) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = (c->direct_iters > 0 || c->small) ? BD_OK : build_step_graph(c);
-  if (rc) return rc;
-  const long long stride = c->total_beads * 3;
-  const double* nz = noise;
-  if (!is_device_ptr(noise)) {
-    if ((rc = ensure_stage(c, (size_t)stride * n_steps))) return rc;
-    CK(cudaMemcpyAsync(c->stage, noise, (size_t)stride * n_steps * sizeof(double),
-                       cudaMemcpyHostToDevice, s));
-    nz = c->stage;
-  }
-  if (c->small && c->direct_iters == 0) {
-    // short FP64 chains: the fused step, all n_steps in one launch on the
-    // context's stream (fenced against the caller's stream like the graph)
-    cudaStream_t cs = c->cs;
-    CK(cudaEventRecord(c->aev[4], s));
-    CK(cudaStreamWaitEvent(cs, c->aev[4], 0));
-    CK(launch_step_small(c->r, c->T, c->status, c->iters, c->state, c->d_cd, c->n_chains, c->max_N, c->ph, nz,
-                         stride, n_steps, c->midpoint, cs));
-    c->small_launches += 1;
-    c->steps_launched += (unsigned long long)n_steps;
-    CK(cudaEventRecord(c->aev[5], cs));
-    CK(cudaStreamWaitEvent(s, c->aev[5], 0));
-    return BD_OK;
-  }
-  CK(launch_set_args(c->args, nz, stride, n_steps, s));
+  const double* nz = nullptr;
+  if (int rc = stage_noise(c, n_steps, noise, s, &nz)) return rc;
   // The steps run on the context's highest-priority stream, ordered after the
   // caller's work on `stream` and before the caller's later work on it (a
   // default-priority caller stream would share the lowest priority with the
   // K chain and lose the factorisation's precedence over it).
-  cudaStream_t cs = c->cs;
   CK(cudaEventRecord(c->aev[4], s));
-  CK(cudaStreamWaitEvent(cs, c->aev[4], 0));
-  if (c->direct_iters > 0) {
-    for (int i = 0; i < n_steps; ++i)
-      if ((rc = enqueue_step_direct(c, cs))) return rc;
-  } else {
-    CK(cudaGraphLaunch(c->exec, cs));  // all n_steps steps in one launch
-    c->steps_launched += (unsigned long long)n_steps;
-  }
-  CK(cudaEventRecord(c->aev[5], cs));
+  if (int rc = launch_steps_locked(c, n_steps, nz, c->total_beads * 3, c->aev[4])) return rc;
   CK(cudaStreamWaitEvent(s, c->aev[5], 0));
   return BD_OK;
 }
 
-int bd_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms_out) {
+static int ctx_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms_out) {
   if (!c || !noise || !ms_out || !is_device_ptr(noise)) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
@@ -1026,7 +1055,7 @@ int bd_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms
   return rc;
 }
 
-int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
+static int ctx_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
   if (!c || !out) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   unsigned long long loops = 0;
@@ -1039,7 +1068,7 @@ int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
   return BD_OK;
 }
 
-int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
+static int ctx_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
   if (!c) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
@@ -1056,7 +1085,7 @@ int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
   return BD_OK;
 }
 
-int bd_chain_status(bd_ctx* c, int* status_host, int* newton_host, void* stream) {
+static int ctx_chain_status(bd_ctx* c, int* status_host, int* newton_host, void* stream) {
   if (!c) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1069,32 +1098,32 @@ int bd_chain_status(bd_ctx* c, int* status_host, int* newton_host, void* stream)
   return worst(st.data(), c->n_chains);
 }
 
-int bd_assemble(bd_ctx* c, void* stream) {
+static int ctx_assemble(bd_ctx* c, void* stream) {
   if (!c) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
   return enqueue_assemble(c, (cudaStream_t)stream);
 }
 
-int bd_factor(bd_ctx* c, void* stream) {
+static int ctx_factor(bd_ctx* c, void* stream) {
   if (!c) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   return enqueue_factor(c, (cudaStream_t)stream);
 }
 
-int bd_brownian(bd_ctx* c, const double* xi_dev, double* y_dev, void* stream) {
+static int ctx_brownian(bd_ctx* c, const double* xi_dev, double* y_dev, void* stream) {
   if (!c || !xi_dev || !y_dev) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   return enqueue_brownian(c, xi_dev, nullptr, y_dev, (cudaStream_t)stream);
 }
 
-int bd_mobility_apply(bd_ctx* c, const double* f_dev, double* u_dev, void* stream) {
+static int ctx_mobility_apply(bd_ctx* c, const double* f_dev, double* u_dev, void* stream) {
   if (!c || !f_dev || !u_dev) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   return enqueue_symv(c, c->M, f_dev, u_dev, nullptr, (cudaStream_t)stream);
 }
 
-int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
+static int ctx_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
   if (!c || !T_dev) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   if (c->total_rods > 0)
@@ -1103,7 +1132,7 @@ int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
   return BD_OK;
 }
 
-int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev, void* stream) {
+static int ctx_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev, void* stream) {
   if (!c || !xi_dev || !rmid_dev || !y_dev || !c->midpoint) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
@@ -1136,7 +1165,7 @@ int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev
   return BD_OK;
 }
 
-int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
+static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
                const double* dJdr_final_dev, double grad_host[2], void* stream) {
   (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
   if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
@@ -1287,7 +1316,7 @@ int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise
   return worst(st.data(), c->n_chains);
 }
 
-int bd_set_factor_config(bd_ctx* c, int panel, int groups) {
+static int ctx_set_factor_config(bd_ctx* c, int panel, int groups) {
   if (!c || !c->mixed || panel < 1 || panel > 96 || groups < 1 || groups > bd_ctx::kMaxGroups)
     return BD_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -1297,7 +1326,11 @@ int bd_set_factor_config(bd_ctx* c, int panel, int groups) {
   return BD_OK;
 }
 
-int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, void* stream) {
+// Shapes bd_tune_factor tries: super-panel widths and chain-group counts.
+static const int kTunePanels[7] = {2, 4, 6, 8, 12, 16, 24};
+static const int kTuneGroups[6] = {1, 2, 4, 8, 12, 16};
+
+static int ctx_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, void* stream) {
   if (!c || !c->mixed) return BD_ERR_ARG;
   if (!c->have_state) return BD_ERR_STATE;
   DeviceGuard g(c->device);
@@ -1305,8 +1338,8 @@ int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, v
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int panels[] = {2, 4, 6, 8, 12, 16, 24};
-  const int groups[] = {1, 2, 4, 8, 12, 16};
+  const int* panels = kTunePanels;
+  const int* groups = kTuneGroups;
   double best = 1e30;
   int bp = c->panel, bg = c->n_groups;
   int rc = BD_OK;
@@ -1345,7 +1378,7 @@ int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, v
   return BD_OK;
 }
 
-int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
+static int ctx_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
   if (!c || !out_host || chain < 0 || chain >= c->n_chains || (which != 0 && which != 1))
     return BD_ERR_ARG;
   DeviceGuard g(c->device);
@@ -1362,7 +1395,7 @@ int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
   return e == cudaSuccess ? BD_OK : BD_ERR_CUDA;
 }
 
-int bd_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
+static int ctx_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
   if (!c || !rel_fro || chain < 0 || chain >= c->n_chains) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   double* acc = nullptr;
@@ -1384,4 +1417,356 @@ int bd_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
   return BD_OK;
 }
 
+// ------------------------------------------------------------ public entry points
+// A context without lanes forwards every call to its ctx_ function.  A context
+// with lanes forwards to each lane with the arrays offset to the lane's first
+// chain, bead or rod; bd_step and the stage calls (assembly, factorisation,
+// Brownian displacement, mobility product, midpoint) fork every lane from one
+// event on the caller's stream and join them back onto it.
+
+// Lane count: p->lanes if given; else 2 for mixed-precision contexts of at
+// least 32 chains, or of at least 4 chains one of which has 2000 beads or
+// more (two concurrent half-batches overlap one half's latency-bound
+// factorisation and per-chain solves with the other half's streaming
+// products; measured faster at 64 and 32 chains of 1000 beads and 4 of 4000,
+// slower at 16 of 1000); else 1.  Never more than the chains; FP64 contexts
+// take one.
+static int lane_count(const bd_params* p) {
+  if (p->precision == BD_FP64) return 1;
+  int max_N = 0;
+  for (int i = 0; i < p->n_chains; ++i) max_N = p->n_beads[i] > max_N ? p->n_beads[i] : max_N;
+  const bool two = p->n_chains >= 32 || (p->n_chains >= 4 && max_N >= 2000);
+  int L = p->lanes > 0 ? p->lanes : (two ? 2 : 1);
+  return L < p->n_chains ? L : p->n_chains;
+}
+
+// First chain of each lane: contiguous ranges of about equal factorisation
+// work (3 N)^3, each of at least one chain.
+static std::vector<int> lane_split(const bd_params* p, int L) {
+  std::vector<double> cum(p->n_chains + 1, 0.0);
+  for (int i = 0; i < p->n_chains; ++i) {
+    const double n = 3.0 * p->n_beads[i];
+    cum[i + 1] = cum[i] + n * n * n;
+  }
+  std::vector<int> c0(L + 1, 0);
+  c0[L] = p->n_chains;
+  for (int l = 1; l < L; ++l) {
+    const double target = cum[p->n_chains] * l / L;
+    int i = c0[l - 1] + 1;
+    while (i < p->n_chains - (L - l) && cum[i] < target) ++i;
+    c0[l] = i;
+  }
+  return c0;
+}
+
+int bd_create(const bd_params* p, bd_ctx** out) {
+  if (!out) return BD_ERR_ARG;
+  *out = nullptr;
+  if (int rc = validate_params(p)) return rc;
+  const int L = lane_count(p);
+  if (L <= 1) return ctx_create(p, out);
+  bd_ctx* c = new (std::nothrow) bd_ctx();
+  if (!c) return BD_ERR_OOM;
+  cudaGetDevice(&c->device);
+  c->p = *p;
+  c->Nc.assign(p->n_beads, p->n_beads + p->n_chains);
+  c->p.n_beads = c->Nc.data();
+  c->n_chains = p->n_chains;
+  c->mixed = true;
+  c->lane_c0 = lane_split(p, L);
+  long long b = 0, r = 0;
+  for (int l = 0; l < L; ++l) {
+    c->lane_b0.push_back(b);
+    c->lane_r0.push_back(r);
+    bd_params q = *p;
+    q.n_chains = c->lane_c0[l + 1] - c->lane_c0[l];
+    q.n_beads = c->Nc.data() + c->lane_c0[l];
+    q.lanes = 1;
+    bd_ctx* sub = nullptr;
+    const int rc = ctx_create(&q, &sub);
+    if (rc) {
+      bd_destroy(c);
+      return rc;
+    }
+    c->lanes.push_back(sub);
+    for (int i = 0; i < q.n_chains; ++i) {
+      b += q.n_beads[i];
+      r += q.n_beads[i] - 1;
+    }
+  }
+  c->total_beads = b;
+  c->total_rods = r;
+  if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    bd_destroy(c);
+    return BD_ERR_CUDA;
+  }
+  *out = c;
+  return BD_OK;
+}
+
+void bd_destroy(bd_ctx* c) {
+  if (!c) return;
+  if (c->lanes.empty()) return ctx_destroy(c);
+  DeviceGuard g(c->device);
+  for (bd_ctx* l : c->lanes) ctx_destroy(l);
+  if (c->stage) cudaFree(c->stage);
+  if (c->fork) cudaEventDestroy(c->fork);
+  delete c;
+}
+
+// Lane holding chain `chain` (the chain's index within it in *local).
+static bd_ctx* lane_of(bd_ctx* c, int chain, int* local) {
+  int l = 0;
+  while (l + 1 < (int)c->lanes.size() && chain >= c->lane_c0[l + 1]) ++l;
+  *local = chain - c->lane_c0[l];
+  return c->lanes[l];
+}
+
+static int more_severe(int w, int r) { return (r != BD_OK && (w == BD_OK || r < w)) ? r : w; }
+
 }  // extern "C"
+
+// Runs fn(lane, index, lane stream) for every lane concurrently: each lane's
+// stream waits for the caller's earlier work on `stream`, and the caller's
+// later work waits for every lane that was started.
+template <typename F>
+static int on_lanes(bd_ctx* c, void* stream, F&& fn) {
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaEventRecord(c->fork, s));
+  int rc = BD_OK;
+  size_t started = 0;
+  for (; started < c->lanes.size(); ++started) {
+    bd_ctx* ln = c->lanes[started];
+    if (cudaStreamWaitEvent(ln->cs, c->fork, 0) != cudaSuccess) {
+      rc = BD_ERR_CUDA;
+      break;
+    }
+    rc = fn(ln, started, (void*)ln->cs);
+    if (cudaEventRecord(ln->aev[5], ln->cs) != cudaSuccess && rc == BD_OK) rc = BD_ERR_CUDA;
+    if (rc) {
+      ++started;
+      break;
+    }
+  }
+  for (size_t l = 0; l < started; ++l)
+    if (cudaStreamWaitEvent(s, c->lanes[l]->aev[5], 0) != cudaSuccess && rc == BD_OK) rc = BD_ERR_CUDA;
+  return rc;
+}
+
+extern "C" {
+
+int bd_set_state(bd_ctx* c, const double* r_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_set_state(c, r_dev, stream);
+  if (!r_dev) return BD_ERR_ARG;
+  for (size_t l = 0; l < c->lanes.size(); ++l)
+    if (int rc = ctx_set_state(c->lanes[l], r_dev + 3 * c->lane_b0[l], stream)) return rc;
+  c->have_state = true;
+  return BD_OK;
+}
+
+int bd_get_state(bd_ctx* c, double* r_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_get_state(c, r_dev, stream);
+  if (!r_dev) return BD_ERR_ARG;
+  for (size_t l = 0; l < c->lanes.size(); ++l)
+    if (int rc = ctx_get_state(c->lanes[l], r_dev + 3 * c->lane_b0[l], stream)) return rc;
+  return BD_OK;
+}
+
+int bd_step(bd_ctx* c, int n_steps, const double* noise, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_step(c, n_steps, noise, stream);
+  if (n_steps < 1 || !noise) return BD_ERR_ARG;
+  if (!c->have_state) return BD_ERR_STATE;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* nz = nullptr;
+  if (int rc = stage_noise(c, n_steps, noise, s, &nz)) return rc;
+  CK(cudaEventRecord(c->fork, s));
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    bd_ctx* ln = c->lanes[l];
+    std::lock_guard<std::mutex> ll(ln->mu);
+    if (int rc = launch_steps_locked(ln, n_steps, nz + 3 * c->lane_b0[l], c->total_beads * 3, c->fork)) return rc;
+  }
+  for (bd_ctx* ln : c->lanes) CK(cudaStreamWaitEvent(s, ln->aev[5], 0));
+  return BD_OK;
+}
+
+int bd_profile_step(bd_ctx* c, const double* noise, int newton_iters, double* ms_out) {
+  if (!c || c->lanes.empty()) return ctx_profile_step(c, noise, newton_iters, ms_out);
+  if (!noise || !ms_out) return BD_ERR_ARG;
+  for (int k = 0; k < 8; ++k) ms_out[k] = 0.0;
+  for (size_t l = 0; l < c->lanes.size(); ++l) {  // lane after lane
+    double ms[8];
+    if (int rc = ctx_profile_step(c->lanes[l], noise + 3 * c->lane_b0[l], newton_iters, ms)) return rc;
+    for (int k = 0; k < 8; ++k) ms_out[k] += ms[k];
+  }
+  return BD_OK;
+}
+
+int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_kernel_launches(c, out, stream);
+  if (!out) return BD_ERR_ARG;
+  unsigned long long tot = 0;
+  for (bd_ctx* l : c->lanes) {
+    unsigned long long v = 0;
+    if (int rc = ctx_kernel_launches(l, &v, stream)) return rc;
+    tot += v;
+  }
+  *out = tot;
+  return BD_OK;
+}
+
+int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_observables(c, obs, status_host, stream);
+  int w = BD_OK;
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    const int c0 = c->lane_c0[l];
+    w = more_severe(w, ctx_observables(c->lanes[l], obs ? obs + (size_t)c0 * BD_OBS_STRIDE : nullptr,
+                                       status_host ? status_host + c0 : nullptr, stream));
+  }
+  return w;
+}
+
+int bd_chain_status(bd_ctx* c, int* status_host, int* newton_host, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_chain_status(c, status_host, newton_host, stream);
+  int w = BD_OK;
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    const int c0 = c->lane_c0[l];
+    w = more_severe(w, ctx_chain_status(c->lanes[l], status_host ? status_host + c0 : nullptr,
+                                        newton_host ? newton_host + c0 : nullptr, stream));
+  }
+  return w;
+}
+
+int bd_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
+  if (!c || c->lanes.empty()) return ctx_factor_residual(c, chain, rel_fro);
+  if (chain < 0 || chain >= c->n_chains) return BD_ERR_ARG;
+  int local = 0;
+  bd_ctx* l = lane_of(c, chain, &local);
+  return ctx_factor_residual(l, local, rel_fro);
+}
+
+int bd_read_matrix(bd_ctx* c, int chain, int which, double* out_host) {
+  if (!c || c->lanes.empty()) return ctx_read_matrix(c, chain, which, out_host);
+  if (chain < 0 || chain >= c->n_chains) return BD_ERR_ARG;
+  int local = 0;
+  bd_ctx* l = lane_of(c, chain, &local);
+  return ctx_read_matrix(l, local, which, out_host);
+}
+
+int bd_assemble(bd_ctx* c, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_assemble(c, stream);
+  return on_lanes(c, stream, [&](bd_ctx* l, size_t, void* ls) { return ctx_assemble(l, ls); });
+}
+
+int bd_factor(bd_ctx* c, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_factor(c, stream);
+  return on_lanes(c, stream, [&](bd_ctx* l, size_t, void* ls) { return ctx_factor(l, ls); });
+}
+
+int bd_brownian(bd_ctx* c, const double* xi_dev, double* y_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_brownian(c, xi_dev, y_dev, stream);
+  if (!xi_dev || !y_dev) return BD_ERR_ARG;
+  return on_lanes(c, stream, [&](bd_ctx* l, size_t k, void* ls) {
+    const long long o = 3 * c->lane_b0[k];
+    return ctx_brownian(l, xi_dev + o, y_dev + o, ls);
+  });
+}
+
+int bd_mobility_apply(bd_ctx* c, const double* f_dev, double* u_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_mobility_apply(c, f_dev, u_dev, stream);
+  if (!f_dev || !u_dev) return BD_ERR_ARG;
+  return on_lanes(c, stream, [&](bd_ctx* l, size_t k, void* ls) {
+    const long long o = 3 * c->lane_b0[k];
+    return ctx_mobility_apply(l, f_dev + o, u_dev + o, ls);
+  });
+}
+
+int bd_get_tensions(bd_ctx* c, double* T_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_get_tensions(c, T_dev, stream);
+  if (!T_dev) return BD_ERR_ARG;
+  for (size_t l = 0; l < c->lanes.size(); ++l)
+    if (int rc = ctx_get_tensions(c->lanes[l], T_dev + c->lane_r0[l], stream)) return rc;
+  return BD_OK;
+}
+
+int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_midpoint(c, xi_dev, rmid_dev, y_dev, stream);
+  if (!xi_dev || !rmid_dev || !y_dev) return BD_ERR_ARG;
+  return on_lanes(c, stream, [&](bd_ctx* l, size_t k, void* ls) {
+    const long long o = 3 * c->lane_b0[k];
+    return ctx_midpoint(l, xi_dev + o, rmid_dev + o, y_dev + o, ls);
+  });
+}
+
+int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
+               const double* dJdr_final_dev, double grad_host[2], void* stream) {
+  // lanes exist on mixed-precision contexts only, which have no tangents
+  if (c && !c->lanes.empty()) return BD_ERR_ARG;
+  return ctx_adjoint(c, r0_dev, n_steps, noise_dev, ckpt_every, dJdr_final_dev, grad_host, stream);
+}
+
+int bd_set_factor_config(bd_ctx* c, int panel, int groups) {
+  if (!c || c->lanes.empty()) return ctx_set_factor_config(c, panel, groups);
+  for (bd_ctx* l : c->lanes)
+    if (int rc = ctx_set_factor_config(l, panel, groups)) return rc;
+  return BD_OK;
+}
+
+int bd_tune_factor(bd_ctx* c, int* panel_out, int* groups_out, double* ms_out, void* stream) {
+  if (!c || c->lanes.empty()) return ctx_tune_factor(c, panel_out, groups_out, ms_out, stream);
+  if (!c->have_state) return BD_ERR_STATE;
+  // every shape is timed with all lanes factoring concurrently, as in the
+  // step (measured a little faster than tuning each lane alone)
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int min_chains = c->n_chains;
+  for (bd_ctx* l : c->lanes) min_chains = l->n_chains < min_chains ? l->n_chains : min_chains;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return BD_ERR_CUDA;
+  }
+  double best = 1e30;
+  int bp = 0, bg = 0;
+  int rc = BD_OK;
+  for (int gi = 0; gi < 6 && rc == BD_OK; ++gi) {
+    if (kTuneGroups[gi] > min_chains) continue;
+    for (int pi = 0; pi < 7 && rc == BD_OK; ++pi) {
+      for (bd_ctx* l : c->lanes)
+        if (!rc) rc = ctx_set_factor_config(l, kTunePanels[pi], kTuneGroups[gi]);
+      float tot = 0.f;
+      for (int rep = 0; rep < 3 && rc == BD_OK; ++rep) {  // first repetition warms up
+        if ((rc = bd_assemble(c, stream))) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (!rc) rc = bd_factor(c, stream);
+        if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = BD_ERR_CUDA;
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BD_ERR_CUDA;
+        if (rep > 0) tot += ms;
+      }
+      if (!rc && tot / 2 < best) {
+        best = tot / 2;
+        bp = kTunePanels[pi];
+        bg = kTuneGroups[gi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  for (bd_ctx* l : c->lanes)
+    if ((rc = ctx_set_factor_config(l, bp, bg))) return rc;
+  if (panel_out) *panel_out = bp;
+  if (groups_out) *groups_out = bg;
+  if (ms_out) *ms_out = best;
+  return BD_OK;
+}
+
+}  // extern "C"
+

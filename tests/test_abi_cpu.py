@@ -47,7 +47,7 @@ def test_strerror_and_defaults(lib):
     lib.bd_params_default(ctypes.byref(p))
     assert p.n_chains == 1 and p.h_star == 0.25 and p.dt == 1e-4 and p.tol == 1e-13
     assert p.max_newton == 50 and p.precision == 0
-    assert p.constraint == 0 and p.k_spring == 1e4 and p.scheme == 0
+    assert p.constraint == 0 and p.k_spring == 1e4 and p.scheme == 0 and p.lanes == 0
 
 
 @pytest.mark.parametrize("mutate", [
@@ -70,6 +70,8 @@ def test_strerror_and_defaults(lib):
     lambda p, nb: setattr(p, "tol", float("nan")),
     lambda p, nb: setattr(p, "constraint", 2),
     lambda p, nb: (setattr(p, "constraint", 1), setattr(p, "k_spring", 0.0)),  # Fraenkel needs K* > 0
+    lambda p, nb: setattr(p, "lanes", -1),
+    lambda p, nb: setattr(p, "lanes", 9),   # at most 8 concurrent sub-batches
 ])
 def test_create_rejects_bad_arguments_before_any_device_call(lib, mutate):
     from paper_2208_06559_gb300 import binding

@@ -295,3 +295,54 @@ def test_step_brownian_displacement_matches_stage_api(bd):
     err = np.abs(dr - y).max() / np.abs(y).max()
     assert err < 1e-6, err
     ctx.close()
+
+
+def test_lanes_equal_one_batch(bd):
+    """A context of 64 uneven chains stepped as 1, 2 or 3 lanes (concurrent
+    sub-batches over contiguous chain ranges, each on its own streams) gives
+    every chain the result of the single batch: positions, tensions,
+    observables and statuses after five steps in one call (host noise), the
+    stage calls (assembly, factorisation, Brownian displacement, mobility
+    product) and one profiled step.  Lanes of other sizes may pick other
+    cluster sizes for the per-chain solves (a different summation order), so
+    the bound is far below any misplaced chain or bead and far above
+    round-off: 1e-8 of the step's displacement."""
+    g = np.random.default_rng(71)
+    Nc = g.integers(20, 61, 64).astype(np.int32)
+    total = int(Nc.sum())
+    r0 = inputs.random_walk(Nc, 72)
+    noise_h = torch.from_numpy(inputs.gaussian_noise(5, total, 73))
+    xi = cuda(inputs.gaussian_noise(2, total, 74))
+    res = {}
+    for lanes in (1, 2, 3):
+        ctx = bd.Context(Nc, precision=bd.MIXED_TF32, flow=1, Wi=10.0, lanes=lanes)
+        ctx.set_state(cuda(r0))
+        ctx.step(noise_h)
+        obs, st = ctx.observables()
+        out = dict(r=ctx.get_state().cpu().numpy(), T=ctx.tensions().cpu().numpy(), obs=obs.cpu().numpy(),
+                   st=st, it=ctx.chain_status()[1], launches=ctx.kernel_launches())
+        ctx.assemble()
+        ctx.factor()
+        out["y"] = ctx.brownian(xi[0]).cpu().numpy()
+        out["u"] = ctx.mobility_apply(xi[1]).cpu().numpy()
+        ms = ctx.profile_step(xi[0])
+        assert ms["step"] > 0.0
+        out["r1"] = ctx.get_state().cpu().numpy()
+        assert (ctx.chain_status()[0] == 0).all()
+        res[lanes] = out
+        ctx.close()
+    ref = res[1]
+    assert (ref["st"] == 0).all() and ref["launches"] > 0
+    disp = np.abs(ref["r"] - r0).max()
+    for lanes in (2, 3):
+        o = res[lanes]
+        assert (o["st"] == ref["st"]).all()
+        assert (np.abs(o["it"] - ref["it"]) <= 1).all()
+        assert o["launches"] > 0
+        assert np.abs(o["r"] - ref["r"]).max() < 1e-8 * disp, lanes
+        assert np.abs(o["r1"] - ref["r1"]).max() < 1e-8 * disp, lanes
+        assert np.abs(o["T"] - ref["T"]).max() < 1e-8 * np.abs(ref["T"]).max(), lanes
+        for k in (bd.OBS_R2, bd.OBS_RG2):
+            np.testing.assert_allclose(o["obs"][:, k], ref["obs"][:, k], rtol=1e-9)
+        assert np.abs(o["y"] - ref["y"]).max() < 1e-8 * np.abs(ref["y"]).max(), lanes
+        assert np.abs(o["u"] - ref["u"]).max() < 1e-10 * np.abs(ref["u"]).max(), lanes
