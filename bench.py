@@ -183,9 +183,11 @@ def run_ours(args, rank, world, local_rank):
         return torch.cuda.Event(enable_timing=True)
 
     tuned = {}
+    lanes_used = {}
 
     def timed_steps(p, nsteps, nwarm):
         ctx = bd.Context(Nc, precision=p, **kw)
+        lanes_used[p] = ctx.lanes()
         ctx.set_state(r0)
         if p != bd.FP64 and not args.no_tune:   # tile shapes of the tensor-core factorisation
             pan, grp, tms = ctx.tune_factor()
@@ -338,6 +340,7 @@ def run_ours(args, rank, world, local_rank):
                        **({"k_spring": w.kspring} if w.constraint == 1 else {}),
                        "precision": "fp64" if prec == bd.FP64 else "mixed_tf32_refined",
                        "l2": f"inputs larger than L2 (per-step matrices {mat_gb:.1f} GB)",
+                       "lanes": lanes_used.get(prec, 1),
                        "parallelism": f"independent replicas x{world}"},
             "roofline": roof, "rooflines_other": others, "stages": stage, "factor_shape": tuned,
             "fp64": fp64,

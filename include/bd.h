@@ -196,6 +196,10 @@ int bd_profile_step(bd_ctx* ctx, const double* noise, int newton_iters, double* 
  * the lanes.  Synchronises the stream. */
 int bd_kernel_launches(bd_ctx* ctx, unsigned long long* out, void* stream);
 
+/* Number of lanes (concurrent sub-batches, see bd_params.lanes) the context
+ * steps its chains in.  Errors: BD_ERR_ARG (NULL). */
+int bd_lanes(bd_ctx* ctx, int* out);
+
 /* Diagnostic: ||B B^T - D||_F / ||D||_F for one chain, from the factor and
  * the D currently held by the context (after bd_factor or bd_step), in FP64
  * on the device.  Synchronises the legacy default stream. */

@@ -85,6 +85,7 @@ EXPORTS = {
     "bd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bd_kernel_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.c_void_p]),
+    "bd_lanes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "bd_profile_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]),
     "bd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -281,6 +282,12 @@ class Context:
         v = ctypes.c_ulonglong()
         _check(lib().bd_kernel_launches(self._h, ctypes.byref(v), _stream(stream)),
                "bd_kernel_launches")
+        return int(v.value)
+
+    def lanes(self) -> int:
+        """Concurrent sub-batches the library steps this context's chains in."""
+        v = ctypes.c_int()
+        _check(lib().bd_lanes(self._h, ctypes.byref(v)), "bd_lanes")
         return int(v.value)
 
     PROFILE_STAGES = ("assemble", "factor", "brownian", "k_wait_predictor", "tension",

@@ -1619,6 +1619,12 @@ int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
   return BD_OK;
 }
 
+int bd_lanes(bd_ctx* c, int* out) {
+  if (!c || !out) return BD_ERR_ARG;
+  *out = c->lanes.empty() ? 1 : (int)c->lanes.size();
+  return BD_OK;
+}
+
 int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
   if (!c || c->lanes.empty()) return ctx_observables(c, obs, status_host, stream);
   int w = BD_OK;

@@ -40,6 +40,9 @@ def main():
     ap.add_argument("--sweep", default="", help="comma-separated bead counts: time one step per N")
     ap.add_argument("--timeline", action="store_true",
                     help="stage-boundary times of one step launched kernel by kernel")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="concurrent sub-batches of a mixed context (0: the library's choice); a "
+                         "timeline of several lanes sums the lanes' times, profiled one after another")
     a = ap.parse_args()
     if a.sweep:
         sweep(a)
@@ -49,7 +52,7 @@ def main():
     Nc = np.full(a.chains, a.beads, np.int32)
     r0 = torch.from_numpy(inputs.random_walk(Nc, a.seed)).cuda()
     ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec,
-                     scheme=bd.SCHEME_MIDPOINT if a.scheme == "midpoint" else bd.SCHEME_EULER)
+                     scheme=bd.SCHEME_MIDPOINT if a.scheme == "midpoint" else bd.SCHEME_EULER, lanes=a.lanes)
     ctx.set_state(r0)
     if prec != bd.FP64 and a.panel > 0:
         bd.lib().bd_set_factor_config(ctx._h, a.panel, a.groups if a.groups > 0 else 1)
@@ -131,7 +134,7 @@ def sweep(a):
     rows = []
     for N in [int(x) for x in a.sweep.split(",")]:
         Nc = np.full(a.chains, N, np.int32)
-        ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec)
+        ctx = bd.Context(Nc, flow=a.flow, Wi=a.Wi, dt=a.dt, precision=prec, lanes=a.lanes)
         ctx.set_state(torch.from_numpy(inputs.random_walk(Nc, a.seed)).cuda())
         xi = torch.from_numpy(inputs.gaussian_noise(a.reps + 1, int(Nc.sum()), a.seed + 1)).cuda()
         ctx.step(xi[0:1])

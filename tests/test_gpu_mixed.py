@@ -316,6 +316,7 @@ def test_lanes_equal_one_batch(bd):
     res = {}
     for lanes in (1, 2, 3):
         ctx = bd.Context(Nc, precision=bd.MIXED_TF32, flow=1, Wi=10.0, lanes=lanes)
+        assert ctx.lanes() == lanes
         ctx.set_state(cuda(r0))
         ctx.step(noise_h)
         obs, st = ctx.observables()
@@ -346,3 +347,19 @@ def test_lanes_equal_one_batch(bd):
             np.testing.assert_allclose(o["obs"][:, k], ref["obs"][:, k], rtol=1e-9)
         assert np.abs(o["y"] - ref["y"]).max() < 1e-8 * np.abs(ref["y"]).max(), lanes
         assert np.abs(o["u"] - ref["u"]).max() < 1e-10 * np.abs(ref["u"]).max(), lanes
+
+
+def test_automatic_lane_count(bd):
+    """Without an explicit count, mixed contexts of >= 32 chains, or of >= 4
+    chains one of which has >= 2000 beads, use two lanes; smaller mixed
+    batches and every FP64 context use one."""
+    cases = [(np.full(64, 30), bd.MIXED_TF32, 2), (np.full(32, 30), bd.MIXED_TF32, 2),
+             (np.full(31, 30), bd.MIXED_TF32, 1), (np.array([30, 30, 30, 2000]), bd.MIXED_TF32, 2),
+             (np.array([30, 30, 1999]), bd.MIXED_TF32, 1), (np.full(64, 30), bd.FP64, 1)]
+    for Nc, prec, want in cases:
+        with bd.Context(Nc.astype(np.int32), precision=prec) as ctx:
+            assert ctx.lanes() == want, (len(Nc), int(Nc.max()), prec)
+    with bd.Context(np.full(8, 30, np.int32), precision=bd.MIXED_TF32, lanes=8) as ctx:
+        assert ctx.lanes() == 8
+    with bd.Context(np.full(3, 30, np.int32), precision=bd.MIXED_TF32, lanes=8) as ctx:
+        assert ctx.lanes() == 3   # never more lanes than chains
