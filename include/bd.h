@@ -120,13 +120,14 @@ typedef struct {
   int refine;            /* mixed precision: 1 = one refinement step on B xi */
   double k_spring;       /* BD_FRAENKEL: spring constant K* > 0 (Eq. (3)); unused for BD_RIGID */
   int scheme;            /* bd_scheme of the rigid-rod step (BD_RIGID only) */
-  int lanes;             /* mixed precision: concurrent sub-batches (lanes) the chains are split into,
-                            contiguous ranges of about equal factorisation work, each stepped by its
-                            own graph on its own streams; 0 = automatic (2 from 32 chains, or from
-                            4 chains when one has >= 2000 beads; else 1), 1..8 (at most n_chains);
-                            FP64 contexts always use 1.  A chain's result depends on the lanes only
-                            through the shapes chosen for its per-chain kernels (summation order).
-                            Out of range: BD_ERR_ARG */
+  int lanes;             /* concurrent sub-batches (lanes) the chains are split into, contiguous
+                            ranges of about equal factorisation work, each stepped by its own graph
+                            on its own streams; 1..8 (at most n_chains), or 0 = automatic: mixed
+                            precision 2 from 32 chains, or from 4 chains when one has >= 2000 beads,
+                            else 1; FP64 one per 16 chains up to 8, and 1 for rigid-rod batches of
+                            chains of <= 32 beads (one fused kernel steps them).  A chain's result
+                            depends on the lanes only through the shapes chosen for its per-chain
+                            kernels (summation order).  Out of range: BD_ERR_ARG */
 } bd_params;
 
 /* Fill *p with defaults: 1 chain (n_beads NULL), h* = 0.25, a = h*, dt = 1e-4,
@@ -243,7 +244,8 @@ int bd_midpoint(bd_ctx* ctx, const double* xi_dev, double* rmid_dev, double* y_d
  * left at the final state.  With BD_SCHEME_MIDPOINT the tangents also run
  * through the midpoint: z' = -L^{-T} Phi(X)^T xi, the derivative of the
  * tangent-space projection, and D(r_m)' from r_m'.  FP64 rigid-rod contexts
- * with h* > 0 only (else BD_ERR_ARG; such contexts have one lane).
+ * with h* > 0 only (else BD_ERR_ARG).  With lanes, the lanes' steps and
+ * tangents run concurrently and their chains' contributions are summed.
  * Synchronises the stream; returns the most severe chain status. */
 int bd_adjoint(bd_ctx* ctx, const double* r0_dev, int n_steps, const double* noise_dev,
                int ckpt_every, const double* dJdr_final_dev, double grad_host[2], void* stream);

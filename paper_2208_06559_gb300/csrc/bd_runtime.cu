@@ -1165,10 +1165,13 @@ static int ctx_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, doubl
   return BD_OK;
 }
 
-static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
-               const double* dJdr_final_dev, double grad_host[2], void* stream) {
-  (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
-  if (!c || !r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
+// noise of step k at noise_dev + k noise_stride (the context's own 3 sum N,
+// or a parent's when the context is a lane)
+// Enqueues the n_steps primal steps and their tangents on `stream`
+// (adjoint_finish forms the gradient).
+static int adjoint_enqueue(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev,
+                           long long noise_stride, void* stream) {
+  if (!c || !r0_dev || !noise_dev || n_steps < 1) return BD_ERR_ARG;
   if (c->mixed || c->fraenkel || !(c->ph.hstar > 0.0)) return BD_ERR_ARG;
   DeviceGuard g(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
@@ -1218,7 +1221,7 @@ static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const doubl
   const double* udir = mid ? c->umid : c->uhat;
   const size_t b3b = b3 * sizeof(double);
   for (int step = 0; step < n_steps; ++step) {
-    const double* xi = noise_dev + (size_t)step * b3;
+    const double* xi = noise_dev + (size_t)step * (size_t)noise_stride;
     // ---- primal step, intermediates kept (r still holds the old positions)
     if ((rc = enqueue_assemble(c, s))) return rc;
     if ((rc = enqueue_factor(c, s))) return rc;
@@ -1302,6 +1305,16 @@ static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const doubl
     CK(launch_finalize(c->d_cd, c->n_chains, c->total_beads, c->rT, c->r, c->state, c->status, nullptr,
                        s));
   }
+  return BD_OK;
+}
+
+// grad_host[p] = dJ/dr_final . r'_p for the context's chains, after
+// adjoint_enqueue on the same stream; synchronises it and returns the most
+// severe chain status.
+static int adjoint_finish(bd_ctx* c, const double* dJdr_final_dev, double grad_host[2], void* stream) {
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b3 = (size_t)c->total_beads * 3;
   std::vector<double> J(b3), rd(2 * b3);
   CK(cudaMemcpyAsync(J.data(), dJdr_final_dev, b3 * sizeof(double), cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(rd.data(), c->rdot, 2 * b3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1314,6 +1327,14 @@ static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const doubl
     grad_host[p] = (double)acc;
   }
   return worst(st.data(), c->n_chains);
+}
+
+static int ctx_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
+                       const double* dJdr_final_dev, double grad_host[2], void* stream) {
+  (void)ckpt_every;  // forward-mode tangents carry O(1) state: no checkpoints are needed
+  if (!c || !dJdr_final_dev || !grad_host) return BD_ERR_ARG;
+  if (int rc = adjoint_enqueue(c, r0_dev, n_steps, noise_dev, c->total_beads * 3, stream)) return rc;
+  return adjoint_finish(c, dJdr_final_dev, grad_host, stream);
 }
 
 static int ctx_set_factor_config(bd_ctx* c, int panel, int groups) {
@@ -1424,20 +1445,29 @@ static int ctx_factor_residual(bd_ctx* c, int chain, double* rel_fro) {
 // Brownian displacement, mobility product, midpoint) fork every lane from one
 // event on the caller's stream and join them back onto it.
 
-// Lane count: p->lanes if given; else 2 for mixed-precision contexts of at
-// least 32 chains, or of at least 4 chains one of which has 2000 beads or
-// more (two concurrent half-batches overlap one half's latency-bound
+// Lane count: p->lanes if given.  Otherwise, mixed precision: 2 for at
+// least 32 chains, or at least 4 chains one of which has 2000 beads or more
+// (two concurrent half-batches overlap one half's latency-bound
 // factorisation and per-chain solves with the other half's streaming
 // products; measured faster at 64 and 32 chains of 1000 beads and 4 of 4000,
-// slower at 16 of 1000); else 1.  Never more than the chains; FP64 contexts
-// take one.
+// slower at 16 of 1000, and slower with 3 or 4 lanes at 64), else 1.  FP64:
+// one lane per 16 chains, at most 8 (measured faster with 4 lanes at 64
+// chains of 1000 beads and with 8 at 128 uneven chains of 50-500 and at 256
+// of 100), and 1 for rigid-rod batches of chains of at most kSmallMaxN beads,
+// which one fused kernel steps.  Never more lanes than chains.
 static int lane_count(const bd_params* p) {
-  if (p->precision == BD_FP64) return 1;
   int max_N = 0;
   for (int i = 0; i < p->n_chains; ++i) max_N = p->n_beads[i] > max_N ? p->n_beads[i] : max_N;
-  const bool two = p->n_chains >= 32 || (p->n_chains >= 4 && max_N >= 2000);
-  int L = p->lanes > 0 ? p->lanes : (two ? 2 : 1);
-  return L < p->n_chains ? L : p->n_chains;
+  int L = p->lanes;
+  if (L <= 0) {
+    if (p->precision == BD_FP64)
+      L = (p->constraint == BD_RIGID && max_N <= kSmallMaxN) ? 1 : p->n_chains / 16;
+    else
+      L = (p->n_chains >= 32 || (p->n_chains >= 4 && max_N >= 2000)) ? 2 : 1;
+  }
+  L = L < kMaxLanes ? L : kMaxLanes;
+  L = L < p->n_chains ? L : p->n_chains;
+  return L > 1 ? L : 1;
 }
 
 // First chain of each lane: contiguous ranges of about equal factorisation
@@ -1472,7 +1502,7 @@ int bd_create(const bd_params* p, bd_ctx** out) {
   c->Nc.assign(p->n_beads, p->n_beads + p->n_chains);
   c->p.n_beads = c->Nc.data();
   c->n_chains = p->n_chains;
-  c->mixed = true;
+  c->mixed = p->precision != BD_FP64;
   c->lane_c0 = lane_split(p, L);
   long long b = 0, r = 0;
   for (int l = 0; l < L; ++l) {
@@ -1710,9 +1740,39 @@ int bd_midpoint(bd_ctx* c, const double* xi_dev, double* rmid_dev, double* y_dev
 
 int bd_adjoint(bd_ctx* c, const double* r0_dev, int n_steps, const double* noise_dev, int ckpt_every,
                const double* dJdr_final_dev, double grad_host[2], void* stream) {
-  // lanes exist on mixed-precision contexts only, which have no tangents
-  if (c && !c->lanes.empty()) return BD_ERR_ARG;
-  return ctx_adjoint(c, r0_dev, n_steps, noise_dev, ckpt_every, dJdr_final_dev, grad_host, stream);
+  if (!c || c->lanes.empty())
+    return ctx_adjoint(c, r0_dev, n_steps, noise_dev, ckpt_every, dJdr_final_dev, grad_host, stream);
+  if (!r0_dev || !noise_dev || !dJdr_final_dev || !grad_host || n_steps < 1) return BD_ERR_ARG;
+  // J's gradient is a sum over chains: every lane contributes its chains'
+  // part; the lanes' steps and tangents run concurrently on their streams,
+  // each reading its beads of the caller's arrays
+  DeviceGuard dg(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaEventRecord(c->fork, s));
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    bd_ctx* ln = c->lanes[l];
+    const long long o = 3 * c->lane_b0[l];
+    CK(cudaStreamWaitEvent(ln->cs, c->fork, 0));
+    if (int rc = adjoint_enqueue(ln, r0_dev + o, n_steps, noise_dev + o, c->total_beads * 3, (void*)ln->cs)) {
+      for (size_t k = 0; k <= l; ++k) cudaStreamSynchronize(c->lanes[k]->cs);
+      return rc;
+    }
+  }
+  int w = BD_OK;
+  double g[2] = {0.0, 0.0};
+  for (size_t l = 0; l < c->lanes.size(); ++l) {
+    double gl[2] = {0.0, 0.0};
+    const int rc = adjoint_finish(c->lanes[l], dJdr_final_dev + 3 * c->lane_b0[l], gl, (void*)c->lanes[l]->cs);
+    if (rc == BD_ERR_CUDA) return rc;
+    w = more_severe(w, rc);
+    g[0] += gl[0];
+    g[1] += gl[1];
+  }
+  grad_host[0] = g[0];
+  grad_host[1] = g[1];
+  c->have_state = true;
+  return w;
 }
 
 int bd_set_factor_config(bd_ctx* c, int panel, int groups) {

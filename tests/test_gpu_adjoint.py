@@ -138,3 +138,25 @@ def test_adjoint_uneven_batch_workload(bd):
     fdo = ((Jo(wi + FD, HS) - Jo(wi - FD, HS)) / (2 * FD), (Jo(wi, HS + FD) - Jo(wi, HS - FD)) / (2 * FD))
     for got, want in zip((gws, ghs), fdo):
         assert abs(got - want) <= 1e-6 * abs(want), (got, want)
+
+
+def test_adjoint_with_lanes_equals_one_batch(bd):
+    """An FP64 context split into 2 or 3 lanes (concurrent sub-batches)
+    returns the gradient of the single batch: every lane contributes its
+    chains' part, reading its beads of the caller's noise; the final states
+    agree as well."""
+    Nc = np.array([12, 20, 7, 16, 9, 25], np.int32)
+    r0 = inputs.random_walk(Nc, 511)
+    noise = inputs.gaussian_noise(10, int(Nc.sum()), 512)
+    r_fin = gpu_run(bd, r0, noise, WI, HS, 0, Nc)
+    _, dJdr = stretch_and_grad(r_fin, Nc)
+    res = {}
+    for lanes in (1, 2, 3):
+        ctx = bd.Context(Nc, h_star=HS, dt=DT, flow=bd.FLOW_UNIAXIAL, Wi=WI, lanes=lanes)
+        assert ctx.lanes() == lanes
+        g = ctx.adjoint(torch.from_numpy(r0).cuda(), torch.from_numpy(noise).cuda(), torch.from_numpy(dJdr).cuda())
+        res[lanes] = (np.array(g), ctx.get_state().cpu().numpy())
+        ctx.close()
+    for lanes in (2, 3):
+        np.testing.assert_allclose(res[lanes][0], res[1][0], rtol=1e-10)
+        np.testing.assert_allclose(res[lanes][1], res[1][1], rtol=0, atol=1e-12)

@@ -351,11 +351,13 @@ def test_lanes_equal_one_batch(bd):
 
 def test_automatic_lane_count(bd):
     """Without an explicit count, mixed contexts of >= 32 chains, or of >= 4
-    chains one of which has >= 2000 beads, use two lanes; smaller mixed
-    batches and every FP64 context use one."""
+    chains one of which has >= 2000 beads, use two lanes, smaller mixed
+    batches one; FP64 contexts use one lane per 16 chains up to 8, and one
+    when every chain has <= 32 beads (the fused short-chain step)."""
     cases = [(np.full(64, 30), bd.MIXED_TF32, 2), (np.full(32, 30), bd.MIXED_TF32, 2),
              (np.full(31, 30), bd.MIXED_TF32, 1), (np.array([30, 30, 30, 2000]), bd.MIXED_TF32, 2),
-             (np.array([30, 30, 1999]), bd.MIXED_TF32, 1), (np.full(64, 30), bd.FP64, 1)]
+             (np.array([30, 30, 1999]), bd.MIXED_TF32, 1), (np.full(64, 30), bd.FP64, 1),
+             (np.full(64, 40), bd.FP64, 4), (np.full(31, 40), bd.FP64, 1), (np.full(256, 33), bd.FP64, 8)]
     for Nc, prec, want in cases:
         with bd.Context(Nc.astype(np.int32), precision=prec) as ctx:
             assert ctx.lanes() == want, (len(Nc), int(Nc.max()), prec)
