@@ -252,7 +252,10 @@ __global__ void __launch_bounds__(128, 3) k_tc_gemm(const CUtensorMap* __restric
           tma_store_2d(om, src, k0 * NB + 32 * q, ti * NB);
       }
       bulk_commit();
-      bulk_wait_all();
+      // the panel solve only needs the staged tile read before it reuses the
+      // shared memory for the FP16 copy; its last wait covers both stores
+      if (MODE == TC_TRSM) bulk_wait_read_all();
+      else bulk_wait_all();
     } else {
       atomicCAS(status + c, BD_OK, BD_ERR_TIMEOUT);
     }
