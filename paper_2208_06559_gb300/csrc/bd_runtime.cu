@@ -1657,6 +1657,10 @@ int bd_lanes(bd_ctx* c, int* out) {
 
 int bd_observables(bd_ctx* c, double* obs, int* status_host, void* stream) {
   if (!c || c->lanes.empty()) return ctx_observables(c, obs, status_host, stream);
+  if (!status_host)  // asynchronous: every lane's kernel and copy on its own stream
+    return on_lanes(c, stream, [&](bd_ctx* l, size_t k, void* ls) {
+      return ctx_observables(l, obs ? obs + (size_t)c->lane_c0[k] * BD_OBS_STRIDE : nullptr, nullptr, ls);
+    });
   int w = BD_OK;
   for (size_t l = 0; l < c->lanes.size(); ++l) {
     const int c0 = c->lane_c0[l];

@@ -320,6 +320,10 @@ def test_lanes_equal_one_batch(bd):
         ctx.set_state(cuda(r0))
         ctx.step(noise_h)
         obs, st = ctx.observables()
+        obs_host = torch.empty((len(Nc), bd.OBS_STRIDE), dtype=torch.float64).pin_memory()
+        ctx.observables(out=obs_host, with_status=False)   # asynchronous, into host memory
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(obs_host.numpy(), obs.cpu().numpy())
         out = dict(r=ctx.get_state().cpu().numpy(), T=ctx.tensions().cpu().numpy(), obs=obs.cpu().numpy(),
                    st=st, it=ctx.chain_status()[1], launches=ctx.kernel_launches())
         ctx.assemble()
