@@ -275,6 +275,18 @@ int bd_set_factor_config(bd_ctx* ctx, int panel, int groups);  /* 1 <= panel <= 
  * diagonal).  Synchronises the legacy default stream. */
 int bd_read_matrix(bd_ctx* ctx, int chain, int which, double* out_host);
 
+/* ---- self-test of the bounded device wait ----
+ * Every wait of the library's kernels on an mbarrier (TMA arrivals, tensor-core
+ * commits) is bounded: after 4e9 SM clock cycles (about two seconds) it gives up, the kernel
+ * records BD_ERR_TIMEOUT in the chain's status word and unwinds, and the CUDA
+ * context stays usable.  This call runs that wait in one thread on the current
+ * device: with arrive = 0 nothing completes the barrier's phase and
+ * *status_host receives BD_ERR_TIMEOUT after the limit (about two seconds);
+ * with arrive != 0 the thread arrives first and it receives BD_OK.  Returns
+ * BD_OK when the kernel ran (synchronising the legacy default stream);
+ * errors: BD_ERR_ARG (NULL), BD_ERR_OOM, BD_ERR_CUDA. */
+int bd_selftest_bounded_wait(int arrive, int* status_host);
+
 /* ---- allocation-free entry point ----
  * The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory (code inside a host framework that owns all device

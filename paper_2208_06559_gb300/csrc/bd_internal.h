@@ -245,6 +245,9 @@ bool make_k_maps(CUtensorMap* host_maps, float* K, const ChainDesc* h_cd, int n_
 cudaError_t launch_kupdate_tc(const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains, int max_mp, int k,
                               int* status, cudaStream_t s);
 bool is_kupdate_tc_kernel(const void* f);
+// One thread waits on an mbarrier that completes only if `arrive`; *out:
+// BD_OK, or BD_ERR_TIMEOUT once the bounded wait gives up.
+cudaError_t launch_wait_selftest(int arrive, int* out, cudaStream_t s);
 // Factor chains [0, n_chains) of the given arrays (pointers may be offset to
 // a chain subrange); wmap is the TMA map of Winv; maps16 map the FP16 copies
 // of the off-diagonal L tiles (same layout as M), written by the panel

@@ -1649,6 +1649,20 @@ int bd_kernel_launches(bd_ctx* c, unsigned long long* out, void* stream) {
   return BD_OK;
 }
 
+int bd_selftest_bounded_wait(int arrive, int* status_host) {
+  if (!status_host) return BD_ERR_ARG;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return BD_ERR_OOM;
+  }
+  cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) e = launch_wait_selftest(arrive != 0, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(status_host, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? BD_OK : BD_ERR_CUDA;
+}
+
 int bd_lanes(bd_ctx* c, int* out) {
   if (!c || !out) return BD_ERR_ARG;
   *out = c->lanes.empty() ? 1 : (int)c->lanes.size();

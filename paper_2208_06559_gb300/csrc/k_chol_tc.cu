@@ -495,6 +495,25 @@ __global__ void __launch_bounds__(128, 3) k_tc_kupdate(const CUtensorMap* __rest
 
 bool is_kupdate_tc_kernel(const void* f) { return f == (const void*)k_tc_kupdate; }
 
+// ------------------------------------------------------------ wait self-test
+// One thread waits on a fresh mbarrier with the bounded wait every kernel of
+// the library uses.  Without an arrival nothing completes the phase and the
+// wait gives up after its limit; *out receives BD_ERR_TIMEOUT (BD_OK when the
+// thread arrived first).
+__global__ void k_wait_selftest(int arrive, int* __restrict__ out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_barrier_init();
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  *out = mbar_wait(&bar, 0) ? BD_OK : BD_ERR_TIMEOUT;
+}
+
+cudaError_t launch_wait_selftest(int arrive, int* out, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(arrive, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kupdate_tc(const CUtensorMap* kmaps, const ChainDesc* cd, int n_chains, int max_mp, int k,
                               int* status, cudaStream_t s) {
   const int r0 = 64 * (k + 1);

@@ -87,6 +87,7 @@ def test_create_rejects_bad_arguments_before_any_device_call(lib, mutate):
     assert lib.bd_create(None, ctypes.byref(h)) == binding.BD_ERR_ARG
     assert lib.bd_step(None, 1, None, None) == binding.BD_ERR_ARG
     assert lib.bd_profile_step(None, None, 0, None) == binding.BD_ERR_ARG
+    assert lib.bd_selftest_bounded_wait(0, None) == binding.BD_ERR_ARG
     lib.bd_destroy(None)
 
 
